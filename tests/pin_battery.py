@@ -1,0 +1,209 @@
+"""A fast battery of the oracle's pins, runnable against any build of the
+oracle library (``python -m tests.pin_battery <libpath> <aten_driver>``).
+
+Used by the mutation test: each planted mistake in the oracle must make at
+least one of these checks fail, and the unmodified oracle must pass them all.
+Prints one JSON list of the failed check names.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import subprocess
+import sys
+
+import numpy as np
+
+import oracle
+from paper_2604_27162_gb300 import workloads as W
+from tests import defcheck
+
+
+def _philox(L, drv):
+    rng = np.random.default_rng(1)
+    cases = [tuple(int(v) for v in rng.integers(0, 2**32, size=6)) for _ in range(64)]
+    cases.append((0, 0, 0, 0, 0, 0))
+    data = "\n".join(" ".join(map(str, c)) for c in cases) + "\n"
+    out = subprocess.run([drv], input=data, capture_output=True, text=True, check=True).stdout
+    ref = [tuple(int(v) for v in ln.split()) for ln in out.strip().splitlines()]
+    return all(tuple(int(v) for v in oracle.philox4x32_10(c[:4], c[4:], L=L)) == r
+               for c, r in zip(cases, ref))
+
+
+def _actions(L):
+    from scipy.stats import chi2
+
+    acts = np.array([oracle.action(5, t, a, e, L=L) for t in range(120) for a in range(6)
+                     for e in range(12)])
+    if acts.min() != 0 or acts.max() != 4:
+        return False
+    cnt = np.bincount(acts, minlength=5).astype(float)
+    exp = cnt.sum() / 5
+    if chi2.sf(((cnt - exp) ** 2 / exp).sum(), 4) <= 1e-4:
+        return False
+    # consecutive steps of one agent are independent (25 equiprobable pairs)
+    b0 = np.array([oracle.action(5, t, 2, e, L=L) for t in range(200) for e in range(12)])
+    b1 = np.array([oracle.action(5, t + 1, 2, e, L=L) for t in range(200) for e in range(12)])
+    cnt = np.bincount(b0 * 5 + b1, minlength=25).astype(float)
+    exp = cnt.sum() / 25
+    if chi2.sf(((cnt - exp) ** 2 / exp).sum(), 24) <= 1e-4:
+        return False
+    # keying convention: word t&3 of the block at counter (t>>2, agent, env, 0)
+    key = [5, 0]
+    for t, a, e in ((0, 0, 0), (5, 3, 7), (10, 1, 2), (3, 9, 11)):
+        u = int(oracle.philox4x32_10([t >> 2, a, e, 0], key, L=L)[t & 3])
+        if oracle.action(5, t, a, e, L=L) != (u * 5) >> 32:
+            return False
+    return True
+
+
+def _moves(L):
+    rng = np.random.default_rng(2)
+    S = 3
+    cells = [(x, y) for y in range(S) for x in range(S)]
+    for mask in range(0, 512, 37):
+        grid = np.array([(mask >> i) & 1 for i in range(9)], np.uint8).reshape(S, S)
+        free = [c for c in cells if not grid[c[1], c[0]]]
+        for p0, p1 in itertools.permutations(free, 2):
+            for a0, a1 in itertools.product(range(5), range(5)):
+                nx, ny = oracle.move(S, grid.reshape(-1), [p0[0], p1[0]], [p0[1], p1[1]],
+                                     [a0, a1], L=L)
+                if list(zip(nx.tolist(), ny.tolist())) != defcheck.moves(
+                        S, grid.tolist(), [p0, p1], [a0, a1]):
+                    return False
+    for _ in range(800):
+        S = int(rng.integers(2, 6))
+        A = int(rng.integers(3, min(6, S * S) + 1))
+        grid = (rng.random((S, S)) < 0.25).astype(np.uint8)
+        cc = rng.permutation(S * S)[:A]
+        grid.reshape(-1)[cc] = 0
+        pos = [(int(c % S), int(c // S)) for c in cc]
+        act = [int(v) for v in rng.integers(0, 5, size=A)]
+        nx, ny = oracle.move(S, grid.reshape(-1), [p[0] for p in pos], [p[1] for p in pos],
+                             act, L=L)
+        if list(zip(nx.tolist(), ny.tolist())) != defcheck.moves(S, grid.tolist(), pos, act):
+            return False
+    return True
+
+
+def _rewards(L):
+    rng = np.random.default_rng(3)
+    if list(oracle.reward(1, 3, [5, 8, 9, 2, 8], [5, 5, 5, 1, 8], L=L)) != [2, -1, 0, 0, -1]:
+        return False
+    for _ in range(500):
+        S = int(rng.integers(2, 12))
+        A = int(rng.integers(1, min(10, S * S) + 1))
+        ns = int(rng.integers(0, A + 1))
+        r = int(rng.integers(0, 5))
+        cc = rng.permutation(S * S)[:A]
+        pos = [(int(c % S), int(c // S)) for c in cc]
+        got = oracle.reward(ns, r, [p[0] for p in pos], [p[1] for p in pos], L=L).tolist()
+        if got != defcheck.rewards(ns, r, pos):
+            return False
+    return True
+
+
+def _observations(L):
+    rng = np.random.default_rng(4)
+    for S in (2, 5, 8):
+        for r in (1, 2, 3, 4):
+            Wd = ((2 * r + 1) ** 2 + 63) // 64
+            for _ in range(6):
+                A = int(rng.integers(2, min(6, S * S) + 1))
+                ns = int(rng.integers(1, A))
+                grid = (rng.random((S, S)) < 0.3).astype(np.uint8)
+                cc = rng.permutation(S * S)[:A]
+                grid.reshape(-1)[cc] = 0
+                pos = [(int(c % S), int(c // S)) for c in cc]
+                for a in range(A):
+                    got = oracle.observe_agent(S, grid.reshape(-1), ns, [p[0] for p in pos],
+                                               [p[1] for p in pos], a, r, L=L)
+                    want = defcheck.observation(S, grid.tolist(), pos, ns, a, r)
+                    for q in range(3):
+                        if [int(v) for v in got[q]] != defcheck.words_of(want[q], Wd):
+                            return False
+    return True
+
+
+def _generation(L):
+    desc = W.ten1k()["descs"][0]
+    n = 96
+    w = oracle.World(n, 2, [desc], L=L)
+    st = w.state()
+    blocked = cells = pairs = both = 0
+    for e in range(n):
+        g = w.grid(e)
+        sx = st["sx"][e * 10:(e + 1) * 10]
+        sy = st["sy"][e * 10:(e + 1) * 10]
+        if len(set(zip(sx.tolist(), sy.tolist()))) != 10 or g[sy, sx].any():
+            return False
+        m = np.ones_like(g, dtype=bool)
+        m[sy, sx] = False
+        blocked += int(g[m].sum())
+        cells += int(m.sum())
+        h = m[:, :-1] & m[:, 1:]
+        both += int((g[:, :-1] & g[:, 1:])[h].sum())
+        pairs += int(h.sum())
+    p = 0.2
+    if abs(blocked / cells - p) > 4 * (p * (1 - p) / cells) ** 0.5:
+        return False
+    q = p * p
+    return abs(both / pairs - q) < 4 * (q * (1 - q) / pairs) ** 0.5
+
+
+def _run(L):
+    desc = dict(W.ten1k()["descs"][0], cap=20)
+    n = 6
+    w = oracle.World(n, 2, [desc], L=L)
+    st0 = w.state()
+    grids = [w.grid(e) for e in range(n)]
+    for t in range(45):
+        prev = w.state()
+        out = w.step()
+        st = w.state()
+        for e in range(n):
+            sl = slice(e * 10, (e + 1) * 10)
+            xs, ys = st["x"][sl], st["y"][sl]
+            d = int(out["done"][e])
+            if d != (3 if (t + 1) % 20 == 0 else 0):
+                return False
+            if d and ((xs != st0["x"][sl]).any() or (ys != st0["y"][sl]).any()):
+                return False
+            act = out["action"][sl].tolist()
+            ppos = list(zip(prev["x"][sl].tolist(), prev["y"][sl].tolist()))
+            if not d and defcheck.moves(32, grids[e].tolist(), ppos, act) != list(
+                    zip(xs.tolist(), ys.tolist())):
+                return False
+            if act != [oracle.action(2, t, a, e, L=L) for a in range(10)]:
+                return False
+    w.reset()
+    s1 = w.state()
+    return all((st0[k] == s1[k]).all() for k in ("x", "y", "ep_t", "ep_idx"))
+
+
+CHECKS = {
+    "philox": None,
+    "actions": _actions,
+    "moves": _moves,
+    "rewards": _rewards,
+    "observations": _observations,
+    "generation": _generation,
+    "run": _run,
+}
+
+
+def battery(L, drv):
+    failed = []
+    for name, fn in CHECKS.items():
+        try:
+            ok = _philox(L, drv) if name == "philox" else fn(L)
+        except Exception:  # noqa: BLE001 - a crash of a check is a failure
+            ok = False
+        if not ok:
+            failed.append(name)
+    return failed
+
+
+if __name__ == "__main__":
+    L = oracle.load_library(sys.argv[1])
+    print(json.dumps(battery(L, sys.argv[2])))

@@ -1,0 +1,101 @@
+"""Mutation test of the oracle's pins (CPU only).
+
+Each mutant plants one plausible mistake in a copy of the oracle's C source
+(a dropped term, a wrong sign or index, a transposed operand), builds it with
+gcc in a temporary directory and runs the pin battery against it in a child
+process.  Every mutant must fail at least one pin; the unmodified oracle must
+pass them all.  The mistakes are planted in the oracle, on the CPU only.
+"""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "hase_oracle.c")
+
+MUTANTS = [
+    ("philox multipliers transposed", "uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;",
+     "uint64_t p0 = (uint64_t)PHILOX_M1 * (uint64_t)c0;"),
+    ("philox hi/lo transposed", "uint32_t n1 = (uint32_t)p1;", "uint32_t n1 = (uint32_t)(p1 >> 32);"),
+    ("philox key bump dropped", "k1 += PHILOX_W1;", "k1 += 0u;"),
+    ("philox xor term dropped", "^ c3 ^ k1;", "^ k1;"),
+    ("action word index", "return mulhi32(out[t & 3u], 5u);", "return mulhi32(out[0], 5u);"),
+    ("action range", "return mulhi32(out[t & 3u], 5u);", "return mulhi32(out[t & 3u], 4u);"),
+    ("action counter transposed", "philox_words(seed, (uint32_t)(t >> 2), agent, env_id, 0u, out);",
+     "philox_words(seed, (uint32_t)(t >> 2), env_id, agent, 0u, out);"),
+    ("north sign", "static const int32_t DY[5] = {0, -1, 1, 0, 0};",
+     "static const int32_t DY[5] = {0, 1, -1, 0, 0};"),
+    ("occupancy check dropped", "if (x[b] == tx[a] && y[b] == ty[a]) ok[a] = 0;", ";"),
+    ("obstacle check dropped", "if (ok[a] && grid[(size_t)ty[a] * S + (size_t)tx[a]] != 0) ok[a] = 0;",
+     ";"),
+    ("highest index wins", "for (uint32_t b = 0; b < a && moves; ++b) {",
+     "for (uint32_t b = a + 1; b < A && moves; ++b) {"),
+    ("reward strict distance", "if (cheb <= (int32_t)r_seek) seen = 1;",
+     "if (cheb < (int32_t)r_seek) seen = 1;"),
+    ("reward hider sign", "rew[h] = seen ? -1 : 0;", "rew[h] = seen ? 1 : 0;"),
+    ("obs index transposed", "uint32_t k = (uint32_t)((dy + R) * D + (dx + R));",
+     "uint32_t k = (uint32_t)((dx + R) * D + (dy + R));"),
+    ("obs out-of-bounds not obstacle", "                out[0 * W + word] |= bit;\n                continue;",
+     "                continue;"),
+    ("obs self not excluded", "                if (b == a) continue;\n", ""),
+    ("obs planes swapped", "                    out[1 * W + word] |= bit;\n                else\n                    out[2 * W + word] |= bit;",
+     "                    out[2 * W + word] |= bit;\n                else\n                    out[1 * W + word] |= bit;"),
+    ("done one step early", "if (w->ep_t[e] == p->cap) {", "if (w->ep_t[e] + 1 == p->cap) {"),
+    ("reset keeps positions", "            w->x[base + a] = w->sx[base + a];\n            w->y[base + a] = w->sy[base + a];\n        }\n    }\n    if (rew)",
+     "        }\n    }\n    if (rew)"),
+    ("start cells not forced free", "for (uint32_t a = 0; a < p->n_agents; ++a) g[cells[a]] = 0;", ";"),
+    ("start duplicates allowed", "if (cells[b] == cell) dup = 1;", ";"),
+    ("obstacle word index", "g[c] = out[c % 4u] < p->density_thr ? 1 : 0;",
+     "g[c] = out[0] < p->density_thr ? 1 : 0;"),
+]
+
+
+@pytest.fixture(scope="module")
+def aten_driver(tmp_path_factory):
+    import torch
+
+    from tests.test_oracle_pins import _ATEN_DRIVER
+
+    d = tmp_path_factory.mktemp("aten")
+    src = d / "drv.cpp"
+    exe = d / "drv"
+    src.write_text(_ATEN_DRIVER)
+    inc = os.path.join(os.path.dirname(torch.__file__), "include")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-I", inc, str(src), "-o", str(exe)])
+    return str(exe)
+
+
+def _build(src_text, d):
+    c = d / "m.c"
+    so = d / "libm.so"
+    c.write_text(src_text)
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", "-I",
+                           os.path.join(ROOT, "oracle"), str(c), "-o", str(so)])
+    return str(so)
+
+
+def _battery(so, drv):
+    out = subprocess.run([sys.executable, "-m", "tests.pin_battery", so, drv], cwd=ROOT,
+                         capture_output=True, text=True, timeout=120)
+    if out.returncode != 0:
+        return ["crashed"]
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def test_unmodified_oracle_passes_battery(tmp_path, aten_driver):
+    so = _build(open(SRC).read(), tmp_path)
+    assert _battery(so, aten_driver) == []
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(name, old, new, tmp_path, aten_driver):
+    text = open(SRC).read()
+    assert text.count(old) == 1, name
+    so = _build(text.replace(old, new), tmp_path)
+    failed = _battery(so, aten_driver)
+    assert failed, "mutant not caught: " + name
