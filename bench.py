@@ -1,0 +1,371 @@
+"""Benchmark of the batched hide-and-seek environment step on GB300.
+
+One benchmark step is one rollout of the workload's run length through the
+whole hot path (actions, moves, collisions, observations, rewards, done,
+auto-reset): for the default workload (1024 envs, 32x32, 5 seekers + 5
+hiders) that is 10,000 env-steps of all 1024 envs.  Every env-step writes its
+outputs into a 10,000-slot ring (2.9 GB, far above the 129 MB L2), so the
+written bytes stream to HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the oracle on the host cores)
+
+Prints one JSON line.  Multi-GPU (torchrun, one rank per GPU): every rank
+steps its own independent env range (weak scaling, no collective on the
+data path); rank 0 reports the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2604_27162_gb300 import workloads as W  # noqa: E402
+
+# Rollout length of one benchmark step per workload (the workload's run).
+RUN_STEPS = {"plain16": 1000, "single1k": 10000, "ten1k": 10000, "uneven64k": 1000}
+
+
+def algorithmic_bytes_per_env_step(descs, n_envs, unpacked):
+    """Bytes the method must deliver per env-step (obs + reward + done, and
+    the unpacked export when requested); padding bits are counted inside the
+    obs words, the CTA-resident state is not (it is read once per launch)."""
+    total = 0
+    for e in range(n_envs):
+        d = descs[0 if len(descs) == 1 else e]
+        wmax = 0
+        n_obs = 0
+        unp = 0
+        for a in range(d["n_agents"]):
+            team = 0 if a < d["n_seekers"] else 1
+            if not (d["obs_teams"] >> team) & 1:
+                continue
+            r = d["r_seek"] if team == 0 else d["r_hide"]
+            D = 2 * r + 1
+            wmax = max(wmax, (D * D + 63) // 64)
+            n_obs += 1
+            unp += 3 * D * D
+        total += n_obs * 3 * wmax * 8 + d["n_agents"] * 4 + 1 + (unp if unpacked else 0)
+    return total / n_envs
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def workload(name):
+    c = W.WORKLOADS[name]()
+    return c
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_27162_gb300 import hase
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    hase.load()
+    c = workload(args.workload)
+    n_envs = c["n_envs"]
+    run = RUN_STEPS[args.workload]
+    flags = hase.HASE_EXPORT_UNPACKED if c["unpacked"] else 0
+    # weak scaling: rank r steps envs [r*E, (r+1)*E) of the global batch
+    stream = torch.cuda.current_stream()
+    eng = hase.Engine(n_envs, c["seed"], c["descs"], ring_steps=run, flags=flags,
+                      env_id_base=rank * n_envs, stream=stream)
+    info = eng.launch_info()
+    spl = info["steps_per_launch"] or 65536
+    launches_per_step = math.ceil(run / spl)
+
+    def one_step():
+        eng.step(run)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    env_steps = n_envs * run * args.steps * world
+    agents = sum(c["descs"][0 if len(c["descs"]) == 1 else e]["n_agents"] for e in range(n_envs))
+    value = env_steps / (ms / 1e3)
+    bpe = algorithmic_bytes_per_env_step(c["descs"], n_envs, c["unpacked"])
+    per_rank_bytes = bpe * n_envs * run * args.steps
+    achieved = per_rank_bytes / (ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the public API: every step's results copied to
+    # pinned host memory inside the timed region (no per-step inputs exist:
+    # actions are drawn on the device)
+    e2e = run_e2e(eng, c, run, stream, args)
+    eng.close()
+    if rank == 0:
+        out = {
+            "metric": "env-steps/s",
+            "value": value,
+            "unit": "env-steps/s",
+            "agent_steps_per_s": value * agents / n_envs,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u32",
+            "data": "synthetic (seeded Bernoulli maps, Philox actions)",
+            "config": {
+                "workload": args.workload,
+                "n_envs_per_gpu": n_envs,
+                "env_steps_per_bench_step": run,
+                "descs": c["descs"] if len(c["descs"]) == 1 else "per-env table (%d)" % n_envs,
+                "ring_steps": run,
+                "l2": "outputs larger than L2 (ring %.2f GB)" % (per_rank_bytes / args.steps / 1e9),
+                "ctas": info["ctas"],
+                "threads_per_cta": info["threads"],
+                "smem_per_cta": info["smem"],
+                "parallelism": "env shards, one process per GPU" if world > 1 else "1 GPU",
+            },
+            "roofline": {
+                "bound": "hbm",
+                "kernel": "step_kernel",
+                "achieved": achieved,
+                "peak": peak,
+                "peak_kind": peak_kind,
+                "unit": "GB/s",
+                "frac": achieved / peak,
+                "algorithmic_bytes_per_env_step": bpe,
+                "traffic": None,
+            },
+            "gpu_launches": args.steps * launches_per_step,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu_baseline(c, args) if world == 1 and not args.no_cpu else None,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(eng, c, run, stream, args):
+    import torch
+
+    n_steps = run * max(1, min(args.steps, 3))
+    chunk = min(1000, run)
+    L = eng.layout
+    h_obs = torch.empty((chunk, L["obs_words"]), dtype=torch.int64, pin_memory=True)
+    h_rew = torch.empty((chunk, L["agents"]), dtype=torch.int32, pin_memory=True)
+    h_done = torch.empty((chunk, eng.n_envs), dtype=torch.uint8, pin_memory=True)
+    h_unp = (torch.empty((chunk, L["unp_bytes"]), dtype=torch.uint8, pin_memory=True)
+             if eng.unpacked is not None else None)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    done_steps = 0
+    while done_steps < n_steps:
+        n = min(chunk, n_steps - done_steps)
+        s = eng.t % eng.ring
+        eng.step(n)
+        idx = [(s + i) % eng.ring for i in range(n)]
+        lo = idx[0]
+        if lo + n <= eng.ring:
+            h_obs[:n].copy_(eng.obs[lo:lo + n], non_blocking=True)
+            h_rew[:n].copy_(eng.reward[lo:lo + n], non_blocking=True)
+            h_done[:n].copy_(eng.done[lo:lo + n], non_blocking=True)
+            if h_unp is not None:
+                h_unp[:n].copy_(eng.unpacked[lo:lo + n], non_blocking=True)
+        else:
+            for j, sl in enumerate(idx):
+                h_obs[j].copy_(eng.obs[sl], non_blocking=True)
+                h_rew[j].copy_(eng.reward[sl], non_blocking=True)
+                h_done[j].copy_(eng.done[sl], non_blocking=True)
+                if h_unp is not None:
+                    h_unp[j].copy_(eng.unpacked[sl], non_blocking=True)
+        done_steps += n
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    d2h = L["obs_words"] * 8 + L["agents"] * 4 + eng.n_envs + (L["unp_bytes"] if h_unp is not None else 0)
+    return {"value": eng.n_envs * n_steps / (ms / 1e3), "unit": "env-steps/s",
+            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h),
+            "note": "per env-step: every env's obs, reward and done copied to pinned host memory"}
+
+
+def cpu_baseline(c, args, target_s=12.0):
+    """The oracle (single-threaded C, as it stands) on a bounded sample of the
+    same workload: all envs of the batch for as many steps as fit ~target_s."""
+    import oracle
+
+    n = c["n_envs"]
+    w = oracle.World(n, c["seed"], c["descs"])
+    t = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t < target_s:
+        w.step(unpacked=c["unpacked"])
+        steps += 1
+    dt = time.perf_counter() - t
+    return {"value": n * steps / dt, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d envs x %d steps of the workload (%.1f s)" % (n, steps, dt)}
+
+
+def run_reference(args):
+    """Reference arm: the oracle timed on the host cores, same metric."""
+    import oracle
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    c = workload(args.workload)
+    n = c["n_envs"]
+    # bounded sample: each benchmark step runs a sample of the rollout, sized
+    # so that warmup + steps take about a minute in total
+    probe = oracle.World(n, c["seed"], c["descs"])
+    t = time.perf_counter()
+    probe.step(unpacked=c["unpacked"])
+    per_env_step = (time.perf_counter() - t) / n
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    sample_envs = max(1, min(n, int(budget / max(per_env_step, 1e-9))))
+    sample_steps = 1
+    w = oracle.World(sample_envs, c["seed"], c["descs"][:1] if len(c["descs"]) == 1 else
+                     c["descs"][:sample_envs])
+    for _ in range(args.warmup):
+        w.step(unpacked=c["unpacked"])
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(sample_steps):
+            w.step(unpacked=c["unpacked"])
+    dt = time.perf_counter() - t
+    value = sample_envs * sample_steps * args.steps / dt
+    out = {
+        "impl": "reference",
+        "metric": "env-steps/s",
+        "value": value,
+        "unit": "env-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic (seeded Bernoulli maps, Philox actions)",
+        "config": {"workload": args.workload, "n_envs_per_gpu": n},
+        "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d of %d envs, 1 env-step per benchmark step" % (sample_envs, n)},
+        "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ten1k", choices=sorted(RUN_STEPS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

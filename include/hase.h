@@ -1,0 +1,179 @@
+/*
+ * hase.h -- C ABI of the GB300-native batched hide-and-seek environment step
+ * (Hide-And-Seek-Engine, arxiv 2604.27162).
+ *
+ * One handle owns a batch of independent grid environments resident in GPU
+ * memory.  hase_step advances every environment by n steps on the caller's
+ * CUDA stream; each step performs, per environment and agent (paper Sec. 3.1
+ * Dec-POMDP with per-agent actions, observations and rewards):
+ *   a1  random actions: Philox4x32-10 (Salmon et al., SC'11) keyed by the
+ *       seed, counter (t >> 2, agent, env, 0), word t & 3, mapped to
+ *       {0 stay, 1 N, 2 S, 3 E, 4 W} as floor(u * 5 / 2^32)  [Sec. 4.1]
+ *   a2  move proposal on the grid; blocking tiles are impassable [Sec. 3.2]
+ *   a3  collisions: a move into any currently occupied cell is blocked; of
+ *       the valid movers with one target the lowest agent index moves
+ *   a5  decentralized observation [Sec. 3.3, mode 1]: a (2r+1)^2 window
+ *       centred on the agent, three planes (0 obstacle or outside the grid,
+ *       1 ally other than the agent itself, 2 opponent), window cell
+ *       (dx, dy) at bit k = (dy + r)(2r + 1) + (dx + r), LSB first, plane p
+ *       in words [p*W, (p+1)*W) with W = ceil((2 r_max + 1)^2 / 64)
+ *   a6  reward: every seeker gets +(number of hiders within Chebyshev
+ *       distance r_seek of some seeker), every such hider -1
+ *   a7  episode counter, truncation at the cap (done byte = 3: bit 0 done,
+ *       bit 1 truncated)
+ *   a8  same-step auto-reset to the pristine start cells [Sec. 4.2]; the
+ *       step's reward and done describe the finished step, its observation
+ *       the reset state.
+ * Creation (a0) draws each env's start cells (counter (attempt, agent, env,
+ * 2), word 0, cell floor(u * S^2 / 2^32), redrawn while taken) and obstacles
+ * (cell c blocked iff word c%4 of counter (c/4, 0, env, 1) < density_thr),
+ * start cells forced free.
+ *
+ * Memory: every buffer lives in device memory and is owned by the handle.
+ * Outputs of global step t (0-based, counted since create or reset) sit in
+ * ring slot t mod ring_steps; the observation of the state after create or
+ * reset ("step -1") sits in slot ring_steps - 1 with zero reward and done.
+ * Layout of one slot (hase_layout gives the sizes and per-env offsets):
+ *   obs      uint64 [obs_words]  env e at obs_off[e]: [A_obs(e)][3][W(e)]
+ *   reward   int32  [agents]     env e at agent_off[e]: [A(e)]
+ *   done     uint8  [n_envs]
+ *   actions  uint8  [agents]     (only with HASE_EXPORT_ACTIONS)
+ *   unpacked uint8  [unp_bytes]  env e at unp_off[e]: [A_obs][3][2r+1][2r+1]
+ *                                (only with HASE_EXPORT_UNPACKED)
+ * A_obs(e) counts the agents whose team emits observations (seekers first).
+ * Pointers returned by the *_ptr calls stay valid until hase_destroy; their
+ * contents are valid once the stream work that wrote them has completed.
+ *
+ * Errors: every call returns a hase_status; the message of the last failure
+ * on a handle is returned by hase_last_error (creation failures by
+ * hase_last_error(NULL)).  No call throws across the ABI.  Launches are
+ * asynchronous: device-side faults surface on a later call or hase_sync as
+ * HASE_ECUDA.
+ */
+#ifndef HASE_H
+#define HASE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hase_status {
+    HASE_OK = 0,
+    HASE_EINVAL = 1,   /* invalid argument or configuration             */
+    HASE_ENOMEM = 2,   /* device or host allocation failed              */
+    HASE_ECUDA = 3,    /* a CUDA runtime call failed                    */
+    HASE_ETIMEOUT = 4, /* a bounded wait ran out                        */
+    HASE_EBUSY = 5,    /* resource temporarily unavailable (admission)  */
+    HASE_ESTATE = 6    /* call not valid in the handle's current state  */
+} hase_status;
+
+/* Limits of this implementation (checked at create). */
+#define HASE_MAX_SIDE 64
+#define HASE_MAX_AGENTS 16
+#define HASE_MAX_RADIUS 4
+
+/* Configuration flags. */
+#define HASE_EXPORT_ACTIONS 1u  /* keep the actions of every step          */
+#define HASE_EXPORT_UNPACKED 2u /* also write the uint8 unpacked obs       */
+
+/* Observation emitters (hase_env_desc.obs_teams). */
+#define HASE_OBS_SEEKERS 1u
+#define HASE_OBS_HIDERS 2u
+
+/* One environment's parameters.  Seekers are agents 0..n_seekers-1, hiders
+ * n_seekers..n_agents-1.  obs_teams = 0 writes no observation (the paper's
+ * "void output" mode). */
+typedef struct hase_env_desc {
+    uint32_t side;        /* grid side S, 2..HASE_MAX_SIDE                   */
+    uint32_t n_agents;    /* A, 1..HASE_MAX_AGENTS, A <= S*S                 */
+    uint32_t n_seekers;   /* 0..A                                            */
+    uint32_t r_seek;      /* seeker view radius 0..HASE_MAX_RADIUS           */
+    uint32_t r_hide;      /* hider view radius 0..HASE_MAX_RADIUS            */
+    uint32_t cap;         /* episode length (steps) >= 1                     */
+    uint32_t density_thr; /* obstacle iff Philox word < density_thr          */
+    uint32_t obs_teams;   /* HASE_OBS_SEEKERS | HASE_OBS_HIDERS              */
+} hase_env_desc;
+
+typedef struct hase_config {
+    uint32_t n_envs;             /* number of environments >= 1                */
+    uint32_t env_id_base;        /* global index of env 0 (Philox counters)    */
+    uint64_t seed;               /* Philox key = (seed & 0xffffffff, seed>>32) */
+    const hase_env_desc *envs;   /* host array of n_desc descriptors           */
+    uint32_t n_desc;             /* 1 (broadcast) or n_envs                    */
+    uint32_t ring_steps;         /* output ring length in steps >= 1           */
+    uint32_t flags;              /* HASE_EXPORT_*                              */
+    uint32_t steps_per_launch;   /* steps fused per kernel launch, 0 = auto    */
+    uint32_t chunk_steps;        /* steps per on-chip chunk (4..32), 0 = auto  */
+    uint32_t emit_warps;         /* output warps per CTA (1..15), 0 = auto     */
+    uint32_t max_group_envs;     /* envs packed per CTA (1..16), 0 = auto      */
+} hase_config;
+
+/* Sizes and per-env offsets of one ring slot.  The offset arrays are host
+ * arrays owned by the handle (n_envs + 1 entries each, valid until
+ * hase_destroy). */
+typedef struct hase_layout {
+    uint32_t n_envs;
+    uint32_t ring_steps;
+    uint64_t agents;         /* reward / action entries per slot            */
+    uint64_t obs_words;      /* uint64 observation words per slot           */
+    uint64_t unp_bytes;      /* unpacked observation bytes per slot         */
+    const uint64_t *agent_off;
+    const uint64_t *obs_off;
+    const uint64_t *unp_off;
+} hase_layout;
+
+typedef struct hase_handle hase_handle;
+
+/* Create a batch on the current CUDA device: validates the configuration,
+ * allocates every buffer, generates the worlds (a0) and writes the step -1
+ * observation, all on `stream` (a cudaStream_t, NULL = legacy default).
+ * Returns HASE_EINVAL for a bad configuration, HASE_ENOMEM when device
+ * memory runs out, HASE_ECUDA for other CUDA errors; *out is NULL then. */
+hase_status hase_create(const hase_config *cfg, void *stream, hase_handle **out);
+
+/* Back to t = 0: start cells, episode counters 0, step -1 observation. */
+hase_status hase_reset(hase_handle *h, void *stream);
+
+/* Enqueue n_steps steps (a1-a9) of every environment on `stream`.
+ * Asynchronous; n_steps = 0 is a no-op. */
+hase_status hase_step(hase_handle *h, uint32_t n_steps, void *stream);
+
+/* Device pointers of the output rings (NULL when the output is not kept). */
+hase_status hase_obs_ptr(hase_handle *h, uint64_t **packed, uint8_t **unpacked);
+hase_status hase_reward_ptr(hase_handle *h, int32_t **reward);
+hase_status hase_done_ptr(hase_handle *h, uint8_t **done);
+hase_status hase_actions_ptr(hase_handle *h, uint8_t **actions);
+hase_status hase_layout_get(hase_handle *h, hase_layout *out);
+
+/* Steps taken since create / reset. */
+hase_status hase_step_count(hase_handle *h, uint64_t *t);
+
+/* Checkpoint: the dynamic state (positions, episode counters, step count)
+ * as an opaque host blob.  hase_get_state with buf = NULL stores the size
+ * in *size.  Both synchronize `stream`. */
+hase_status hase_get_state(hase_handle *h, void *buf, size_t *size, void *stream);
+hase_status hase_set_state(hase_handle *h, const void *buf, size_t size, void *stream);
+
+/* Read back the pristine obstacle grid of env e (side*side bytes, row
+ * major, 1 = obstacle) and the start cells (x, y per agent).  Synchronous. */
+hase_status hase_get_world(hase_handle *h, uint32_t e, uint8_t *grid, int32_t *start_xy);
+
+/* Wait for all work the handle enqueued. */
+hase_status hase_sync(hase_handle *h);
+
+/* Number of CTAs and dynamic shared memory of one step launch, and the
+ * fused steps per launch (for reports and the autotuner). */
+hase_status hase_launch_info(hase_handle *h, uint32_t *ctas, uint32_t *threads,
+                             uint32_t *smem_bytes, uint32_t *steps_per_launch);
+
+void hase_destroy(hase_handle *h);
+const char *hase_last_error(const hase_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

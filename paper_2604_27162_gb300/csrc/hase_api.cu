@@ -1,0 +1,503 @@
+// hase_api.cu -- host side of the C ABI declared in include/hase.h: config
+// validation, HBM layout, CTA grouping, launches, checkpoint blobs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hase.h"
+#include "hase_internal.cuh"
+
+namespace hase {
+cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_envs, uint32_t key0,
+                            uint32_t key1, uint16_t* pos, uint16_t* start, uint64_t* rows, uint32_t* err,
+                            cudaStream_t st);
+cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* pos,
+                           const uint64_t* rows, uint64_t* obs, uint8_t* unp, cudaStream_t st);
+cudaError_t launch_step(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
+                        cudaStream_t st);
+}  // namespace hase
+
+using namespace hase;
+
+struct hase_handle {
+    int device = 0;
+    uint32_t n_envs = 0, ring = 1, flags = 0;
+    uint64_t seed = 0;
+    std::vector<EnvRT> env;
+    std::vector<uint32_t> thr;
+    std::vector<Group> groups;
+    std::vector<uint64_t> agent_off, obs_off, unp_off;
+    uint64_t agents = 0, obs_words = 0, unp_bytes = 0, rows_words = 0;
+    uint32_t smem = 0, threads = 0, kc = 32, emit_warps = 3, steps_per_launch = 0;
+    uint64_t t = 0;
+    // device memory
+    EnvRT* d_env = nullptr;
+    EnvState* d_est = nullptr;
+    uint16_t* d_pos = nullptr;
+    uint16_t* d_start = nullptr;
+    uint64_t* d_rows = nullptr;
+    Group* d_groups = nullptr;
+    uint64_t* d_obs = nullptr;
+    int32_t* d_rew = nullptr;
+    uint8_t* d_done = nullptr;
+    uint8_t* d_act = nullptr;
+    uint8_t* d_unp = nullptr;
+    uint32_t* d_err = nullptr;
+    uint32_t* d_thr = nullptr;
+    std::string err;
+};
+
+static std::string g_create_err;
+
+static hase_status fail(hase_handle* h, hase_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h)
+        h->err = buf;
+    else
+        g_create_err = buf;
+    return st;
+}
+
+static hase_status cuda_fail(hase_handle* h, cudaError_t e, const char* what) {
+    return fail(h, e == cudaErrorMemoryAllocation ? HASE_ENOMEM : HASE_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define HASE_CUDA(h, call)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);   \
+    } while (0)
+
+static void free_all(hase_handle* h) {
+    void* ptrs[] = {h->d_env, h->d_est,  h->d_pos, h->d_start, h->d_rows, h->d_groups,
+                    h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+static bool emits(const hase_env_desc& d, uint32_t a) {
+    const uint32_t team = a < d.n_seekers ? 0u : 1u;
+    return (d.obs_teams >> team) & 1u;
+}
+
+static uint32_t radius(const hase_env_desc& d, uint32_t a) { return a < d.n_seekers ? d.r_seek : d.r_hide; }
+
+static hase_status validate(const hase_env_desc& d, uint32_t i) {
+    if (d.side < 2 || d.side > HASE_MAX_SIDE)
+        return fail(nullptr, HASE_EINVAL, "env desc %u: side %u outside 2..%d", i, d.side, HASE_MAX_SIDE);
+    if (d.n_agents < 1 || d.n_agents > HASE_MAX_AGENTS || d.n_agents > d.side * d.side)
+        return fail(nullptr, HASE_EINVAL, "env desc %u: n_agents %u outside 1..min(%d, side^2)", i,
+                    d.n_agents, HASE_MAX_AGENTS);
+    if (d.n_seekers > d.n_agents)
+        return fail(nullptr, HASE_EINVAL, "env desc %u: n_seekers %u > n_agents %u", i, d.n_seekers,
+                    d.n_agents);
+    if (d.r_seek > HASE_MAX_RADIUS || d.r_hide > HASE_MAX_RADIUS)
+        return fail(nullptr, HASE_EINVAL, "env desc %u: view radius above %d", i, HASE_MAX_RADIUS);
+    if (d.cap < 1) return fail(nullptr, HASE_EINVAL, "env desc %u: episode cap must be >= 1", i);
+    if (d.obs_teams > 3u) return fail(nullptr, HASE_EINVAL, "env desc %u: obs_teams must be 0..3", i);
+    return HASE_OK;
+}
+
+// Consecutive envs are packed into CTA groups while the agents fit one
+// half-warp (16 slots), the env count stays within the limit and all envs
+// use the same row width (so a CTA's row code path is uniform).
+static void make_groups(hase_handle* h, uint32_t max_envs) {
+    h->groups.clear();
+    uint32_t smem_max = 0;
+    uint32_t e = 0;
+    while (e < h->n_envs) {
+        Group g;
+        g.env_first = e;
+        g.n_envs = 0;
+        g.n_slots = 0;
+        uint32_t rows_w = 0, nbr_b = 0;
+        const uint8_t rw = h->env[e].rw;
+        while (e < h->n_envs && g.n_envs < max_envs && h->env[e].rw == rw &&
+               g.n_slots + h->env[e].n_agents <= kMaxSlots) {
+            const EnvRT& E = h->env[e];
+            g.n_slots += E.n_agents;
+            g.n_envs += 1;
+            rows_w += (uint32_t)(E.side + 2 * kPad) * E.rw;
+            nbr_b += (uint32_t)E.side * E.side;
+            ++e;
+        }
+        smem_max = std::max(smem_max, smem_layout(rows_w, nbr_b).total);
+        h->groups.push_back(g);
+    }
+    h->smem = smem_max;
+}
+
+extern "C" {
+
+const char* hase_last_error(const hase_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out) {
+    if (!out) return fail(nullptr, HASE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, HASE_EINVAL, "cfg is NULL");
+    if (cfg->n_envs < 1) return fail(nullptr, HASE_EINVAL, "n_envs must be >= 1");
+    if (!cfg->envs) return fail(nullptr, HASE_EINVAL, "envs is NULL");
+    if (cfg->n_desc != 1 && cfg->n_desc != cfg->n_envs)
+        return fail(nullptr, HASE_EINVAL, "n_desc must be 1 or n_envs");
+    if (cfg->ring_steps < 1) return fail(nullptr, HASE_EINVAL, "ring_steps must be >= 1");
+    if ((uint64_t)cfg->env_id_base + cfg->n_envs > 0x100000000ull)
+        return fail(nullptr, HASE_EINVAL, "env ids exceed 32 bits");
+    if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED))
+        return fail(nullptr, HASE_EINVAL, "unknown flags 0x%x", cfg->flags);
+    if (cfg->chunk_steps != 0 && (cfg->chunk_steps < 1 || cfg->chunk_steps > (uint32_t)kMaxChunk))
+        return fail(nullptr, HASE_EINVAL, "chunk_steps outside 1..%d", kMaxChunk);
+    if (cfg->emit_warps > 15) return fail(nullptr, HASE_EINVAL, "emit_warps outside 1..15");
+    if (cfg->max_group_envs > (uint32_t)kMaxGroupEnvs)
+        return fail(nullptr, HASE_EINVAL, "max_group_envs outside 1..%d", kMaxGroupEnvs);
+    for (uint32_t i = 0; i < cfg->n_desc; ++i) {
+        hase_status s = validate(cfg->envs[i], i);
+        if (s != HASE_OK) return s;
+    }
+
+    hase_handle* h = new hase_handle();
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaGetDevice(&h->device);
+    h->n_envs = cfg->n_envs;
+    h->ring = cfg->ring_steps;
+    h->flags = cfg->flags;
+    h->seed = cfg->seed;
+    h->kc = cfg->chunk_steps ? cfg->chunk_steps : 32;
+    // steps of one chunk are written concurrently: they must own distinct
+    // ring slots, so a chunk never spans more steps than the ring holds
+    h->kc = std::min(h->kc, h->ring);
+    h->emit_warps = cfg->emit_warps ? cfg->emit_warps : 3;
+    h->threads = 32 * (1 + h->emit_warps);
+    h->steps_per_launch = cfg->steps_per_launch;
+
+    h->env.resize(h->n_envs);
+    h->thr.resize(h->n_envs);
+    h->agent_off.assign(h->n_envs + 1, 0);
+    h->obs_off.assign(h->n_envs + 1, 0);
+    h->unp_off.assign(h->n_envs + 1, 0);
+    uint64_t rows = 0;
+    for (uint32_t e = 0; e < h->n_envs; ++e) {
+        const hase_env_desc& d = cfg->envs[cfg->n_desc == 1 ? 0 : e];
+        uint32_t wmax = 0, n_obs = 0;
+        uint64_t unp = 0;
+        for (uint32_t a = 0; a < d.n_agents; ++a) {
+            if (!emits(d, a)) continue;
+            const uint32_t D = 2 * radius(d, a) + 1;
+            wmax = std::max(wmax, (D * D + 63) / 64);
+            n_obs += 1;
+            unp += 3ull * D * D;
+        }
+        EnvRT E;
+        E.side = (uint8_t)d.side;
+        E.n_agents = (uint8_t)d.n_agents;
+        E.n_seekers = (uint8_t)d.n_seekers;
+        E.r_seek = (uint8_t)d.r_seek;
+        E.r_hide = (uint8_t)d.r_hide;
+        E.obs_teams = (uint8_t)d.obs_teams;
+        E.wpp = (uint8_t)wmax;
+        E.rw = (uint8_t)((d.side + 2 * kPad <= 64) ? 1 : 2);
+        E.cap = d.cap;
+        E.agent_off = (uint32_t)h->agent_off[e];
+        E.obs_off = (uint32_t)h->obs_off[e];
+        E.unp_off = (uint32_t)h->unp_off[e];
+        E.rows_off = (uint32_t)rows;
+        E.env_id = cfg->env_id_base + e;
+        h->env[e] = E;
+        h->thr[e] = d.density_thr;
+        h->agent_off[e + 1] = h->agent_off[e] + d.n_agents;
+        h->obs_off[e + 1] = h->obs_off[e] + (uint64_t)n_obs * 3 * wmax;
+        h->unp_off[e + 1] = h->unp_off[e] + unp;
+        rows += (uint64_t)(d.side + 2 * kPad) * E.rw;
+    }
+    h->agents = h->agent_off[h->n_envs];
+    h->obs_words = h->obs_off[h->n_envs];
+    h->unp_bytes = (h->flags & HASE_EXPORT_UNPACKED) ? h->unp_off[h->n_envs] : 0;
+    h->rows_words = rows;
+    if (h->obs_words > 0xffffffffull || h->agents > 0xffffffffull || h->unp_bytes > 0xffffffffull) {
+        delete h;
+        return fail(nullptr, HASE_EINVAL, "per-step output slice exceeds 2^32 entries");
+    }
+    make_groups(h, cfg->max_group_envs ? cfg->max_group_envs : kMaxGroupEnvs);
+
+    auto alloc = [&](void** p, size_t bytes) -> cudaError_t {
+        return cudaMalloc(p, bytes ? bytes : 16);
+    };
+    const uint64_t R = h->ring;
+    cudaError_t ce = cudaSuccess;
+#define HASE_ALLOC(ptr, bytes)                                      \
+    if (ce == cudaSuccess) ce = alloc((void**)&(ptr), (bytes));
+    HASE_ALLOC(h->d_env, sizeof(EnvRT) * h->n_envs);
+    HASE_ALLOC(h->d_est, sizeof(EnvState) * h->n_envs);
+    HASE_ALLOC(h->d_pos, 2 * h->agents);
+    HASE_ALLOC(h->d_start, 2 * h->agents);
+    HASE_ALLOC(h->d_rows, 8 * h->rows_words);
+    HASE_ALLOC(h->d_groups, sizeof(Group) * h->groups.size());
+    HASE_ALLOC(h->d_obs, 8 * R * h->obs_words);
+    HASE_ALLOC(h->d_rew, 4 * R * h->agents);
+    HASE_ALLOC(h->d_done, R * h->n_envs);
+    if (h->flags & HASE_EXPORT_ACTIONS) HASE_ALLOC(h->d_act, R * h->agents);
+    if (h->flags & HASE_EXPORT_UNPACKED) HASE_ALLOC(h->d_unp, R * h->unp_bytes);
+    HASE_ALLOC(h->d_err, 4);
+    HASE_ALLOC(h->d_thr, 4 * h->n_envs);
+#undef HASE_ALLOC
+    if (ce != cudaSuccess) {
+        hase_status s = cuda_fail(nullptr, ce, "cudaMalloc");
+        free_all(h);
+        delete h;
+        return s;
+    }
+    auto finish = [&](cudaError_t e, const char* what) -> hase_status {
+        if (e == cudaSuccess) return HASE_OK;
+        hase_status s = cuda_fail(nullptr, e, what);
+        free_all(h);
+        delete h;
+        return s;
+    };
+    hase_status s;
+    if ((s = finish(cudaMemcpyAsync(h->d_env, h->env.data(), sizeof(EnvRT) * h->n_envs,
+                                    cudaMemcpyHostToDevice, st), "copy env")) != HASE_OK) return s;
+    if ((s = finish(cudaMemcpyAsync(h->d_thr, h->thr.data(), 4 * h->n_envs, cudaMemcpyHostToDevice, st),
+                    "copy thresholds")) != HASE_OK) return s;
+    if ((s = finish(cudaMemcpyAsync(h->d_groups, h->groups.data(), sizeof(Group) * h->groups.size(),
+                                    cudaMemcpyHostToDevice, st), "copy groups")) != HASE_OK) return s;
+    if ((s = finish(cudaMemsetAsync(h->d_est, 0, sizeof(EnvState) * h->n_envs, st), "memset")) != HASE_OK)
+        return s;
+    if ((s = finish(cudaMemsetAsync(h->d_err, 0, 4, st), "memset")) != HASE_OK) return s;
+    if ((s = finish(cudaMemsetAsync(h->d_obs, 0, 8 * R * h->obs_words, st), "memset")) != HASE_OK) return s;
+    if ((s = finish(cudaMemsetAsync(h->d_rew, 0, 4 * R * h->agents, st), "memset")) != HASE_OK) return s;
+    if ((s = finish(cudaMemsetAsync(h->d_done, 0, R * h->n_envs, st), "memset")) != HASE_OK) return s;
+    if (h->d_act && (s = finish(cudaMemsetAsync(h->d_act, 0, R * h->agents, st), "memset")) != HASE_OK)
+        return s;
+    if (h->d_unp && (s = finish(cudaMemsetAsync(h->d_unp, 0, R * h->unp_bytes, st), "memset")) != HASE_OK)
+        return s;
+    const uint32_t key0 = (uint32_t)(h->seed & 0xffffffffu), key1 = (uint32_t)(h->seed >> 32);
+    if ((s = finish(launch_generate(h->d_env, h->d_thr, h->n_envs, key0, key1, h->d_pos, h->d_start, h->d_rows,
+                                    h->d_err, st), "generate")) != HASE_OK)
+        return s;
+    const uint64_t last = R - 1;
+    if ((s = finish(launch_observe(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_obs + last * h->obs_words,
+                                   h->d_unp ? h->d_unp + last * h->unp_bytes : nullptr, st),
+                    "observe")) != HASE_OK)
+        return s;
+    uint32_t herr = 0;
+    if ((s = finish(cudaMemcpyAsync(&herr, h->d_err, 4, cudaMemcpyDeviceToHost, st), "copy err")) != HASE_OK)
+        return s;
+    if ((s = finish(cudaStreamSynchronize(st), "generate sync")) != HASE_OK) return s;
+    if (herr) {
+        free_all(h);
+        delete h;
+        return fail(nullptr, HASE_EINVAL, "start-cell draw did not terminate");
+    }
+    *out = h;
+    return HASE_OK;
+}
+
+hase_status hase_reset(hase_handle* h, void* stream) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t last = h->ring - 1;
+    HASE_CUDA(h, cudaMemcpyAsync(h->d_pos, h->d_start, 2 * h->agents, cudaMemcpyDeviceToDevice, st));
+    HASE_CUDA(h, cudaMemsetAsync(h->d_est, 0, sizeof(EnvState) * h->n_envs, st));
+    HASE_CUDA(h, cudaMemsetAsync(h->d_rew + last * h->agents, 0, 4 * h->agents, st));
+    HASE_CUDA(h, cudaMemsetAsync(h->d_done + last * h->n_envs, 0, h->n_envs, st));
+    if (h->d_act) HASE_CUDA(h, cudaMemsetAsync(h->d_act + last * h->agents, 0, h->agents, st));
+    HASE_CUDA(h, launch_observe(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_obs + last * h->obs_words,
+                                h->d_unp ? h->d_unp + last * h->unp_bytes : nullptr, st));
+    h->t = 0;
+    return HASE_OK;
+}
+
+hase_status hase_step(hase_handle* h, uint32_t n_steps, void* stream) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (n_steps == 0) return HASE_OK;
+    if (((h->t + n_steps) >> 2) > 0xffffffffull)
+        return fail(h, HASE_EINVAL, "step counter would exceed 2^34 (Philox counter word)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t K = h->steps_per_launch ? h->steps_per_launch : 65536u;
+    uint32_t left = n_steps;
+    while (left > 0) {
+        const uint32_t n = std::min(left, K);
+        StepParams p;
+        p.env = h->d_env;
+        p.est = h->d_est;
+        p.pos = h->d_pos;
+        p.start = h->d_start;
+        p.rows = h->d_rows;
+        p.groups = h->d_groups;
+        p.obs = h->d_obs;
+        p.rew = h->d_rew;
+        p.done = h->d_done;
+        p.act_out = h->d_act;
+        p.unp = h->d_unp;
+        p.obs_words = h->obs_words;
+        p.agents = h->agents;
+        p.unp_bytes = h->unp_bytes;
+        p.t0 = h->t;
+        p.n_envs = h->n_envs;
+        p.ring = h->ring;
+        p.slot0 = (uint32_t)(h->t % h->ring);
+        p.n_steps = n;
+        p.kc = h->kc;
+        p.emit_warps = h->emit_warps;
+        p.key0 = (uint32_t)(h->seed & 0xffffffffu);
+        p.key1 = (uint32_t)(h->seed >> 32);
+        HASE_CUDA(h, launch_step(p, (uint32_t)h->groups.size(), h->threads, h->smem, st));
+        h->t += n;
+        left -= n;
+    }
+    return HASE_OK;
+}
+
+hase_status hase_obs_ptr(hase_handle* h, uint64_t** packed, uint8_t** unpacked) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (packed) *packed = h->d_obs;
+    if (unpacked) *unpacked = h->d_unp;
+    return HASE_OK;
+}
+
+hase_status hase_reward_ptr(hase_handle* h, int32_t** reward) {
+    if (!h || !reward) return fail(h, HASE_EINVAL, "NULL argument");
+    *reward = h->d_rew;
+    return HASE_OK;
+}
+
+hase_status hase_done_ptr(hase_handle* h, uint8_t** done) {
+    if (!h || !done) return fail(h, HASE_EINVAL, "NULL argument");
+    *done = h->d_done;
+    return HASE_OK;
+}
+
+hase_status hase_actions_ptr(hase_handle* h, uint8_t** actions) {
+    if (!h || !actions) return fail(h, HASE_EINVAL, "NULL argument");
+    *actions = h->d_act;
+    return HASE_OK;
+}
+
+hase_status hase_layout_get(hase_handle* h, hase_layout* out) {
+    if (!h || !out) return fail(h, HASE_EINVAL, "NULL argument");
+    out->n_envs = h->n_envs;
+    out->ring_steps = h->ring;
+    out->agents = h->agents;
+    out->obs_words = h->obs_words;
+    out->unp_bytes = h->unp_bytes;
+    out->agent_off = h->agent_off.data();
+    out->obs_off = h->obs_off.data();
+    out->unp_off = h->unp_off.data();
+    return HASE_OK;
+}
+
+hase_status hase_step_count(hase_handle* h, uint64_t* t) {
+    if (!h || !t) return fail(h, HASE_EINVAL, "NULL argument");
+    *t = h->t;
+    return HASE_OK;
+}
+
+static const uint64_t kBlobMagic = 0x3130455341484742ull;  // "BGHASE01"
+
+hase_status hase_get_state(hase_handle* h, void* buf, size_t* size, void* stream) {
+    if (!h || !size) return fail(h, HASE_EINVAL, "NULL argument");
+    const size_t need = 4 * 8 + 2 * h->agents + sizeof(EnvState) * h->n_envs;
+    if (!buf) {
+        *size = need;
+        return HASE_OK;
+    }
+    if (*size < need) return fail(h, HASE_EINVAL, "state buffer too small (%zu < %zu)", *size, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t* hdr = (uint64_t*)buf;
+    hdr[0] = kBlobMagic;
+    hdr[1] = h->n_envs;
+    hdr[2] = h->agents;
+    hdr[3] = h->t;
+    uint8_t* p = (uint8_t*)buf + 32;
+    HASE_CUDA(h, cudaMemcpyAsync(p, h->d_pos, 2 * h->agents, cudaMemcpyDeviceToHost, st));
+    HASE_CUDA(h, cudaMemcpyAsync(p + 2 * h->agents, h->d_est, sizeof(EnvState) * h->n_envs,
+                                 cudaMemcpyDeviceToHost, st));
+    HASE_CUDA(h, cudaStreamSynchronize(st));
+    *size = need;
+    return HASE_OK;
+}
+
+hase_status hase_set_state(hase_handle* h, const void* buf, size_t size, void* stream) {
+    if (!h || !buf) return fail(h, HASE_EINVAL, "NULL argument");
+    const size_t need = 4 * 8 + 2 * h->agents + sizeof(EnvState) * h->n_envs;
+    if (size != need) return fail(h, HASE_EINVAL, "state blob has %zu bytes, expected %zu", size, need);
+    const uint64_t* hdr = (const uint64_t*)buf;
+    if (hdr[0] != kBlobMagic || hdr[1] != h->n_envs || hdr[2] != h->agents)
+        return fail(h, HASE_EINVAL, "state blob does not match this handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint8_t* p = (const uint8_t*)buf + 32;
+    // every position must lie on its env's grid (the kernels index by it)
+    for (uint32_t e = 0; e < h->n_envs; ++e) {
+        const EnvRT& E = h->env[e];
+        for (uint32_t a = 0; a < E.n_agents; ++a) {
+            uint16_t q;
+            memcpy(&q, p + 2 * ((size_t)E.agent_off + a), 2);
+            if ((q & 0xffu) >= E.side || (q >> 8) >= E.side)
+                return fail(h, HASE_EINVAL, "state blob: agent %u of env %u off the grid", a, e);
+        }
+    }
+    HASE_CUDA(h, cudaMemcpyAsync(h->d_pos, p, 2 * h->agents, cudaMemcpyHostToDevice, st));
+    HASE_CUDA(h, cudaMemcpyAsync(h->d_est, p + 2 * h->agents, sizeof(EnvState) * h->n_envs,
+                                 cudaMemcpyHostToDevice, st));
+    HASE_CUDA(h, cudaStreamSynchronize(st));
+    h->t = hdr[3];
+    return HASE_OK;
+}
+
+hase_status hase_get_world(hase_handle* h, uint32_t e, uint8_t* grid, int32_t* start_xy) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (e >= h->n_envs) return fail(h, HASE_EINVAL, "env %u out of range", e);
+    const EnvRT& E = h->env[e];
+    const int S = E.side, rw = E.rw;
+    if (grid) {
+        std::vector<uint64_t> rows((size_t)(S + 2 * kPad) * rw);
+        HASE_CUDA(h, cudaMemcpy(rows.data(), h->d_rows + E.rows_off, 8 * rows.size(), cudaMemcpyDeviceToHost));
+        for (int y = 0; y < S; ++y)
+            for (int x = 0; x < S; ++x) {
+                const int b = x + kPad;
+                grid[y * S + x] = (uint8_t)((rows[(size_t)(y + kPad) * rw + (b >> 6)] >> (b & 63)) & 1u);
+            }
+    }
+    if (start_xy) {
+        std::vector<uint16_t> st(E.n_agents);
+        HASE_CUDA(h, cudaMemcpy(st.data(), h->d_start + E.agent_off, 2 * st.size(), cudaMemcpyDeviceToHost));
+        for (int a = 0; a < E.n_agents; ++a) {
+            start_xy[2 * a] = st[a] & 0xff;
+            start_xy[2 * a + 1] = st[a] >> 8;
+        }
+    }
+    return HASE_OK;
+}
+
+hase_status hase_sync(hase_handle* h) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    HASE_CUDA(h, cudaDeviceSynchronize());
+    return HASE_OK;
+}
+
+hase_status hase_launch_info(hase_handle* h, uint32_t* ctas, uint32_t* threads, uint32_t* smem,
+                             uint32_t* steps_per_launch) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (ctas) *ctas = (uint32_t)h->groups.size();
+    if (threads) *threads = h->threads;
+    if (smem) *smem = h->smem;
+    if (steps_per_launch) *steps_per_launch = h->steps_per_launch;
+    return HASE_OK;
+}
+
+void hase_destroy(hase_handle* h) {
+    if (!h) return;
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

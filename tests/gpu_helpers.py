@@ -1,0 +1,61 @@
+"""Helpers of the GPU parity tests: run the CUDA engine through the C ABI and
+the oracle on the same seeded inputs and compare every output bit for bit."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+from paper_2604_27162_gb300 import hase
+
+
+def engine_outputs(eng):
+    import torch
+
+    torch.cuda.synchronize()
+    out = {
+        "obs": eng.obs.cpu().numpy().view(np.uint64),
+        "reward": eng.reward.cpu().numpy(),
+        "done": eng.done.cpu().numpy(),
+    }
+    if eng.actions is not None:
+        out["action"] = eng.actions.cpu().numpy()
+    if eng.unpacked is not None:
+        out["unpacked"] = eng.unpacked.cpu().numpy()
+    return out
+
+
+def compare_run(n_envs, seed, descs, n_steps, ring=None, flags=hase.HASE_EXPORT_ACTIONS,
+                env_id_base=0, launches=None, **tuning):
+    """Step the engine n_steps (in the given launch sizes) and the oracle in
+    lockstep; every slot still in the ring must match exactly."""
+    ring = ring or n_steps + 1
+    eng = hase.Engine(n_envs, seed, descs, ring, flags, env_id_base, **tuning)
+    for n in (launches or [n_steps]):
+        eng.step(n)
+    assert sum(launches or [n_steps]) == n_steps
+    got = engine_outputs(eng)
+    unpacked = bool(flags & hase.HASE_EXPORT_UNPACKED)
+    w = oracle.World(n_envs, seed, descs, env_id_base=env_id_base)
+    if ring > n_steps:
+        init = w.observe(unpacked=unpacked)
+        o0 = init[0] if unpacked else init
+        assert (got["obs"][ring - 1] == o0).all(), "initial observation"
+        if unpacked:
+            assert (got["unpacked"][ring - 1] == init[1]).all(), "initial unpacked"
+        assert (got["reward"][ring - 1] == 0).all() and (got["done"][ring - 1] == 0).all()
+    for t in range(n_steps):
+        o = w.step(unpacked=unpacked)
+        if t < n_steps - ring:
+            continue
+        s = t % ring
+        for k in ("obs", "reward", "done", "action", "unpacked"):
+            if k in got and k in o:
+                if not (got[k][s] == o[k]).all():
+                    bad = np.flatnonzero(got[k][s] != o[k])[:8]
+                    raise AssertionError("%s differs at step %d, entries %s: gpu %s oracle %s" % (
+                        k, t, bad.tolist(), got[k][s][bad].tolist(), o[k][bad].tolist()))
+    st = w.state()
+    eng_t = eng.t
+    eng.close()
+    assert eng_t == n_steps
+    return st

@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA engine (through the C ABI) against the oracle, bit
+for bit on every output of every step (integer and bit work: exact).
+
+Sizes span several CTA groups, chunk boundaries, ring wrap-around and
+episode resets; the full-size runs use the launch configuration of the
+benchmark and compare sampled environments one by one (the oracle steps a
+single env through its global env id) plus properties that hold at any size.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_27162_gb300 import hase
+from paper_2604_27162_gb300 import workloads as W
+from tests.gpu_helpers import compare_run, engine_outputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    hase.load()
+
+
+def test_plain16_full_run():
+    c = W.plain16()
+    compare_run(c["n_envs"], c["seed"], c["descs"], c["steps"])
+
+
+def test_ten_agents_1024_envs_600_steps():
+    c = W.ten1k()
+    compare_run(1024, c["seed"], c["descs"], 600)
+
+
+def test_single_agent_packed_and_unpacked():
+    c = W.single1k()
+    compare_run(1024, c["seed"], c["descs"], 300,
+                flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED)
+
+
+def test_uneven_batch():
+    descs = W.uneven_descs(1500, 3)
+    compare_run(1500, 3, descs, 300)
+
+
+@pytest.mark.parametrize("tuning", [
+    dict(chunk_steps=1, emit_warps=1),
+    dict(chunk_steps=5, emit_warps=2, steps_per_launch=7),
+    dict(chunk_steps=32, emit_warps=7, max_group_envs=1),
+    dict(chunk_steps=13, emit_warps=15, steps_per_launch=1),
+    dict(chunk_steps=4, emit_warps=4, max_group_envs=3),
+])
+def test_launch_configurations_agree(tuning):
+    c = W.ten1k()
+    descs = [dict(c["descs"][0], cap=37)]
+    compare_run(70, c["seed"], descs, 90, **tuning)
+    compare_run(40, 11, W.uneven_descs(40, 5), 90, **tuning)
+
+
+def test_ring_wraparound_and_split_launches():
+    c = W.ten1k()
+    compare_run(64, c["seed"], c["descs"], 300, ring=7, launches=[1, 2, 97, 200])
+    compare_run(64, c["seed"], c["descs"], 50, ring=1, launches=[3, 47])
+
+
+@pytest.mark.parametrize("desc", [
+    W.env_desc(8, 1, 1, 3, 3, 20, "0.15"),            # lone seeker
+    W.env_desc(8, 5, 0, 2, 2, 20, "0.15"),            # hiders only
+    W.env_desc(8, 5, 5, 2, 2, 20, "0.15"),            # seekers only
+    W.env_desc(12, 6, 3, 0, 0, 9, "0.2"),             # radius 0
+    W.env_desc(12, 9, 4, 4, 1, 17, "0.25"),           # radius 4: two words per plane
+    W.env_desc(2, 3, 1, 2, 1, 5, "0.5"),              # smallest grid
+    W.env_desc(64, 16, 8, 4, 4, 33, "0.3"),           # largest grid: two-word rows
+    W.env_desc(57, 7, 3, 3, 2, 40, "0.1"),            # first side with two-word rows
+    W.env_desc(56, 7, 3, 3, 2, 40, "0.1"),            # last side with one-word rows
+    W.env_desc(16, 8, 4, 2, 3, 1, "0.15"),            # cap 1: reset every step
+    W.env_desc(10, 4, 2, 2, 2, 30, 0),                # no obstacles
+    W.env_desc(10, 4, 2, 2, 2, 30, 2**32 - 1),        # all blocked but start cells
+    W.env_desc(4, 16, 8, 1, 2, 30, "0.2"),            # full grid: nobody can move
+    W.env_desc(16, 6, 3, 3, 2, 30, "0.2", 0),         # void observations
+    W.env_desc(16, 6, 3, 3, 2, 30, "0.2", 2),         # hiders only emit
+])
+def test_edge_cases(desc):
+    compare_run(37, 5, [desc], 80, flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED)
+
+
+def test_checkpoint_resume_and_reset_replay():
+    import torch
+
+    c = W.ten1k()
+    eng = hase.Engine(96, c["seed"], c["descs"], 400, hase.HASE_EXPORT_ACTIONS)
+    eng.step(150)
+    blob = eng.get_state()
+    eng.step(150)
+    first = engine_outputs(eng)
+    eng.set_state(blob)
+    assert eng.t == 150
+    eng.step(150)
+    second = engine_outputs(eng)
+    for k in first:
+        assert (first[k][150:300] == second[k][150:300]).all(), k
+    eng.reset()
+    assert eng.t == 0
+    eng.step(300)
+    third = engine_outputs(eng)
+    for k in first:
+        assert (first[k][:300] == third[k][:300]).all(), k
+    torch.cuda.synchronize()
+    eng.close()
+
+
+def test_world_readback_matches_oracle():
+    descs = W.uneven_descs(30, 9)
+    eng = hase.Engine(30, 77, descs, 2)
+    w = oracle.World(30, 77, descs)
+    st = w.state()
+    off = w.agent_off.astype(int)
+    for e in range(30):
+        d = descs[e]
+        grid, start = hase.hase_get_world(eng.h, e, d["side"], d["n_agents"])
+        assert (grid == w.grid(e)).all()
+        assert (start[:, 0] == st["sx"][off[e]:off[e + 1]]).all()
+        assert (start[:, 1] == st["sy"][off[e]:off[e + 1]]).all()
+    eng.close()
+
+
+def test_invalid_configs_rejected():
+    good = W.ten1k()["descs"][0]
+    for bad in (dict(good, side=65), dict(good, side=1), dict(good, n_agents=17),
+                dict(good, n_agents=0), dict(good, n_seekers=11), dict(good, r_seek=5),
+                dict(good, cap=0), dict(good, obs_teams=4)):
+        with pytest.raises(hase.HaseError) as ei:
+            hase.Engine(4, 0, [bad], 2)
+        assert ei.value.status == hase.HASE_EINVAL
+    with pytest.raises(hase.HaseError):
+        hase.Engine(4, 0, [good], 0)
+    with pytest.raises(hase.HaseError):
+        hase.Engine(0, 0, [good], 2)
+
+
+# ---------------------------------------------------------------------------
+# Full-size runs in the benchmark's launch configuration.
+# ---------------------------------------------------------------------------
+def _full_size_check(cfg, n_steps, sample_envs, flags=0):
+    import torch
+
+    n = cfg["n_envs"]
+    descs = cfg["descs"]
+    eng = hase.Engine(n, cfg["seed"], descs, n_steps, flags)
+    eng.step(n_steps)
+    torch.cuda.synchronize()
+    L = eng.layout
+    aoff = L["agent_off"].astype(np.int64)
+    ooff = L["obs_off"].astype(np.int64)
+    # properties over every env and step (on the GPU)
+    done = eng.done
+    caps = torch.tensor([descs[0 if len(descs) == 1 else e]["cap"] for e in range(n)],
+                        device="cuda", dtype=torch.int64)
+    steps = torch.arange(n_steps, device="cuda", dtype=torch.int64)[:, None]
+    want_done = torch.where((steps + 1) % caps[None, :] == 0, 3, 0).to(torch.uint8)
+    assert torch.equal(done, want_done)
+    # sampled envs: every output of every step against a one-env oracle
+    for e in sample_envs:
+        d = descs[0 if len(descs) == 1 else e]
+        rew = eng.reward[:, aoff[e]:aoff[e + 1]].cpu().numpy()
+        obs = eng.obs[:, ooff[e]:ooff[e + 1]].cpu().numpy().view(np.uint64)
+        dn = eng.done[:, e].cpu().numpy()
+        w = oracle.World(1, cfg["seed"], [d], env_id_base=e)
+        for t in range(n_steps):
+            o = w.step()
+            assert (rew[t] == o["reward"]).all(), (e, t)
+            assert (obs[t] == o["obs"]).all(), (e, t)
+            assert dn[t] == o["done"][0], (e, t)
+    eng.close()
+
+
+def test_full_size_ten_agents_sampled():
+    cfg = W.ten1k()
+    _full_size_check(cfg, cfg["steps"], [0, 1, 337, 511, 512, 1023])
+
+
+def test_full_size_single_agent_sampled():
+    cfg = W.single1k()
+    _full_size_check(cfg, 3000, [0, 5, 700, 1023], flags=hase.HASE_EXPORT_UNPACKED)
+
+
+def test_full_size_uneven_sampled():
+    cfg = W.uneven64k()
+    _full_size_check(cfg, 200, [0, 1, 4097, 33333, 65535])
