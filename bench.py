@@ -139,7 +139,7 @@ def run_gpu(args):
     hase.load()
     c = workload(args.workload)
     n_envs = c["n_envs"]
-    run = RUN_STEPS[args.workload]
+    run = args.run_steps or RUN_STEPS[args.workload]
     flags = hase.HASE_EXPORT_UNPACKED if c["unpacked"] else 0
     # weak scaling: rank r steps envs [r*E, (r+1)*E) of the global batch
     stream = torch.cuda.current_stream()
@@ -188,7 +188,7 @@ def run_gpu(args):
     # end to end through the public API: every step's results copied to
     # pinned host memory inside the timed region (no per-step inputs exist:
     # actions are drawn on the device)
-    e2e = run_e2e(eng, c, run, stream, args)
+    e2e = None if args.no_e2e else run_e2e(eng, c, run, stream, args)
     eng.close()
     if rank == 0:
         out = {
@@ -360,6 +360,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ten1k", choices=sorted(RUN_STEPS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--run-steps", type=int, default=0,
+                    help="override the env-steps per benchmark step (small profiling cases)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -92,7 +92,7 @@ typedef struct hase_env_desc {
     uint32_t n_seekers;   /* 0..A                                            */
     uint32_t r_seek;      /* seeker view radius 0..HASE_MAX_RADIUS           */
     uint32_t r_hide;      /* hider view radius 0..HASE_MAX_RADIUS            */
-    uint32_t cap;         /* episode length (steps) >= 1                     */
+    uint32_t cap;         /* episode length (steps), 1..2^31-1               */
     uint32_t density_thr; /* obstacle iff Philox word < density_thr          */
     uint32_t obs_teams;   /* HASE_OBS_SEEKERS | HASE_OBS_HIDERS              */
 } hase_env_desc;
@@ -106,9 +106,9 @@ typedef struct hase_config {
     uint32_t ring_steps;         /* output ring length in steps >= 1           */
     uint32_t flags;              /* HASE_EXPORT_*                              */
     uint32_t steps_per_launch;   /* steps fused per kernel launch, 0 = auto    */
-    uint32_t chunk_steps;        /* steps per on-chip chunk (4..32), 0 = auto  */
-    uint32_t emit_warps;         /* output warps per CTA (1..15), 0 = auto     */
-    uint32_t max_group_envs;     /* envs packed per CTA (1..16), 0 = auto      */
+    uint32_t chunk_steps;        /* steps per on-chip chunk (1..32), 0 = auto  */
+    uint32_t emit_warps;         /* output warps per CTA (1..12), 0 = auto     */
+    uint32_t max_group_envs;     /* envs packed per CTA (1..64), 0 = auto      */
 } hase_config;
 
 /* Sizes and per-env offsets of one ring slot.  The offset arrays are host

@@ -31,9 +31,10 @@ struct hase_handle {
     std::vector<EnvRT> env;
     std::vector<uint32_t> thr;
     std::vector<Group> groups;
+    std::vector<uint32_t> env_list;
     std::vector<uint64_t> agent_off, obs_off, unp_off;
     uint64_t agents = 0, obs_words = 0, unp_bytes = 0, rows_words = 0;
-    uint32_t smem = 0, threads = 0, kc = 32, emit_warps = 3, steps_per_launch = 0;
+    uint32_t smem = 0, threads = 0, kc = 16, emit_warps = 0, steps_per_launch = 0, n_dyn = 1;
     uint64_t t = 0;
     // device memory
     EnvRT* d_env = nullptr;
@@ -42,6 +43,7 @@ struct hase_handle {
     uint16_t* d_start = nullptr;
     uint64_t* d_rows = nullptr;
     Group* d_groups = nullptr;
+    uint32_t* d_env_list = nullptr;
     uint64_t* d_obs = nullptr;
     int32_t* d_rew = nullptr;
     uint8_t* d_done = nullptr;
@@ -80,7 +82,7 @@ static hase_status cuda_fail(hase_handle* h, cudaError_t e, const char* what) {
 
 static void free_all(hase_handle* h) {
     void* ptrs[] = {h->d_env, h->d_est,  h->d_pos, h->d_start, h->d_rows, h->d_groups,
-                    h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr};
+                    h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr, h->d_env_list};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -103,38 +105,83 @@ static hase_status validate(const hase_env_desc& d, uint32_t i) {
                     d.n_agents);
     if (d.r_seek > HASE_MAX_RADIUS || d.r_hide > HASE_MAX_RADIUS)
         return fail(nullptr, HASE_EINVAL, "env desc %u: view radius above %d", i, HASE_MAX_RADIUS);
-    if (d.cap < 1) return fail(nullptr, HASE_EINVAL, "env desc %u: episode cap must be >= 1", i);
+    if (d.cap < 1 || d.cap > 0x7fffffffu)
+        return fail(nullptr, HASE_EINVAL, "env desc %u: episode cap outside 1..2^31-1", i);
     if (d.obs_teams > 3u) return fail(nullptr, HASE_EINVAL, "env desc %u: obs_teams must be 0..3", i);
     return HASE_OK;
 }
 
-// Consecutive envs are packed into CTA groups while the agents fit one
-// half-warp (16 slots), the env count stays within the limit and all envs
-// use the same row width (so a CTA's row code path is uniform).
-static void make_groups(hase_handle* h, uint32_t max_envs) {
+// CTA grouping.  Envs are ordered by their kernel-relevant shape (row width,
+// cell packing, radii, emitting teams, agent and seeker counts) so that every group is
+// uniform, then packed in that order.  With few envs (at most 16 per SM) the
+// envs are spread evenly over one CTA per SM (persistent, balanced); with
+// many envs a group is one dynamics warp (<= 32 agents) and the CTAs run in
+// waves.  Per group the obstacle plane comes from per-cell window tables when
+// they fit the shared-memory budget.
+static uint64_t shape_key(const EnvRT& E) {
+    return ((uint64_t)E.rw << 56) | ((uint64_t)E.r_seek << 48) | ((uint64_t)E.r_hide << 40) |
+           ((uint64_t)E.obs_teams << 32) | ((uint64_t)cell_shift(E) << 24) | ((uint64_t)E.n_agents << 8) |
+           (uint64_t)E.n_seekers;
+}
+
+static void make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
+    const uint32_t E = h->n_envs;
+    h->env_list.resize(E);
+    for (uint32_t e = 0; e < E; ++e) h->env_list[e] = e;
+    std::stable_sort(h->env_list.begin(), h->env_list.end(), [&](uint32_t a, uint32_t b) {
+        return shape_key(h->env[a]) < shape_key(h->env[b]);
+    });
+    uint32_t epc;
+    if (max_envs_cfg)
+        epc = max_envs_cfg;
+    else if (E <= 16u * n_sm)
+        epc = (E + n_sm - 1) / n_sm;
+    else
+        epc = kMaxGroupEnvs;  // bounded by one dynamics warp below
+    const bool many = !max_envs_cfg && E > 16u * n_sm;
     h->groups.clear();
-    uint32_t smem_max = 0;
-    uint32_t e = 0;
-    while (e < h->n_envs) {
+    uint32_t smem_max = 0, dyn_max = 1;
+    GroupPlan plan;
+    std::vector<EnvRT> genv;
+    uint32_t i = 0;
+    while (i < E) {
+        const uint64_t key = shape_key(h->env[h->env_list[i]]);
         Group g;
-        g.env_first = e;
+        g.list_first = i;
         g.n_envs = 0;
         g.n_slots = 0;
-        uint32_t rows_w = 0, nbr_b = 0;
-        const uint8_t rw = h->env[e].rw;
-        while (e < h->n_envs && g.n_envs < max_envs && h->env[e].rw == rw &&
-               g.n_slots + h->env[e].n_agents <= kMaxSlots) {
-            const EnvRT& E = h->env[e];
-            g.n_slots += E.n_agents;
+        g.flags = 0;
+        g.n_dyn = 1;
+        g.pad = 0;
+        genv.clear();
+        while (i < E && g.n_envs < epc && g.n_envs < (uint32_t)kMaxGroupEnvs) {
+            const EnvRT& En = h->env[h->env_list[i]];
+            if (shape_key(En) != key) break;
+            if (g.n_slots + En.n_agents > (uint32_t)kMaxGroupSlots) break;
+            if (many && g.n_slots + En.n_agents > 32u) break;
+            genv.push_back(En);
+            uint16_t flags = 0;
+            if (!plan_group(genv.data(), (int)genv.size(), (int)h->kc, flags, plan) ||
+                plan.total > kSmemBudget) {
+                genv.pop_back();
+                break;
+            }
+            g.n_slots += En.n_agents;
             g.n_envs += 1;
-            rows_w += (uint32_t)(E.side + 2 * kPad) * E.rw;
-            nbr_b += (uint32_t)E.side * E.side;
-            ++e;
+            ++i;
         }
-        smem_max = std::max(smem_max, smem_layout(rows_w, nbr_b).total);
+        uint16_t flags = 0;
+        plan_group(genv.data(), g.n_envs, (int)h->kc, kUseTable, plan);
+        if (plan.total <= kSmemBudget) flags |= kUseTable;
+        plan_group(genv.data(), g.n_envs, (int)h->kc, flags, plan);
+        g.flags = flags;
+        g.n_dyn = (uint8_t)plan.n_dyn;
+        smem_max = std::max(smem_max, plan.total);
+        dyn_max = std::max(dyn_max, plan.n_dyn);
         h->groups.push_back(g);
     }
     h->smem = smem_max;
+    h->n_dyn = dyn_max;
 }
 
 extern "C" {
@@ -156,7 +203,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         return fail(nullptr, HASE_EINVAL, "unknown flags 0x%x", cfg->flags);
     if (cfg->chunk_steps != 0 && (cfg->chunk_steps < 1 || cfg->chunk_steps > (uint32_t)kMaxChunk))
         return fail(nullptr, HASE_EINVAL, "chunk_steps outside 1..%d", kMaxChunk);
-    if (cfg->emit_warps > 15) return fail(nullptr, HASE_EINVAL, "emit_warps outside 1..15");
+    if (cfg->emit_warps > 12) return fail(nullptr, HASE_EINVAL, "emit_warps outside 1..12");
     if (cfg->max_group_envs > (uint32_t)kMaxGroupEnvs)
         return fail(nullptr, HASE_EINVAL, "max_group_envs outside 1..%d", kMaxGroupEnvs);
     for (uint32_t i = 0; i < cfg->n_desc; ++i) {
@@ -175,8 +222,6 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     // steps of one chunk are written concurrently: they must own distinct
     // ring slots, so a chunk never spans more steps than the ring holds
     h->kc = std::min(h->kc, h->ring);
-    h->emit_warps = cfg->emit_warps ? cfg->emit_warps : 3;
-    h->threads = 32 * (1 + h->emit_warps);
     h->steps_per_launch = cfg->steps_per_launch;
 
     h->env.resize(h->n_envs);
@@ -226,7 +271,17 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         delete h;
         return fail(nullptr, HASE_EINVAL, "per-step output slice exceeds 2^32 entries");
     }
-    make_groups(h, cfg->max_group_envs ? cfg->max_group_envs : kMaxGroupEnvs);
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    if (n_sm <= 0) n_sm = 1;
+    make_groups(h, cfg->max_group_envs, (uint32_t)n_sm);
+    // emission warps: enough to fill 16 warps per CTA in the persistent
+    // regime, a few per group when CTAs run in waves
+    if (cfg->emit_warps)
+        h->emit_warps = cfg->emit_warps;
+    else
+        h->emit_warps = h->groups.size() <= (size_t)n_sm ? 12u : 3u;
+    h->threads = 32 * (h->n_dyn + h->emit_warps);
 
     auto alloc = [&](void** p, size_t bytes) -> cudaError_t {
         return cudaMalloc(p, bytes ? bytes : 16);
@@ -241,6 +296,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     HASE_ALLOC(h->d_start, 2 * h->agents);
     HASE_ALLOC(h->d_rows, 8 * h->rows_words);
     HASE_ALLOC(h->d_groups, sizeof(Group) * h->groups.size());
+    HASE_ALLOC(h->d_env_list, 4 * h->n_envs);
     HASE_ALLOC(h->d_obs, 8 * R * h->obs_words);
     HASE_ALLOC(h->d_rew, 4 * R * h->agents);
     HASE_ALLOC(h->d_done, R * h->n_envs);
@@ -267,6 +323,8 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
                                     cudaMemcpyHostToDevice, st), "copy env")) != HASE_OK) return s;
     if ((s = finish(cudaMemcpyAsync(h->d_thr, h->thr.data(), 4 * h->n_envs, cudaMemcpyHostToDevice, st),
                     "copy thresholds")) != HASE_OK) return s;
+    if ((s = finish(cudaMemcpyAsync(h->d_env_list, h->env_list.data(), 4 * h->n_envs, cudaMemcpyHostToDevice, st),
+                    "copy env list")) != HASE_OK) return s;
     if ((s = finish(cudaMemcpyAsync(h->d_groups, h->groups.data(), sizeof(Group) * h->groups.size(),
                                     cudaMemcpyHostToDevice, st), "copy groups")) != HASE_OK) return s;
     if ((s = finish(cudaMemsetAsync(h->d_est, 0, sizeof(EnvState) * h->n_envs, st), "memset")) != HASE_OK)
@@ -333,6 +391,7 @@ hase_status hase_step(hase_handle* h, uint32_t n_steps, void* stream) {
         p.start = h->d_start;
         p.rows = h->d_rows;
         p.groups = h->d_groups;
+        p.env_list = h->d_env_list;
         p.obs = h->d_obs;
         p.rew = h->d_rew;
         p.done = h->d_done;
@@ -348,6 +407,7 @@ hase_status hase_step(hase_handle* h, uint32_t n_steps, void* stream) {
         p.n_steps = n;
         p.kc = h->kc;
         p.emit_warps = h->emit_warps;
+        p.n_dyn = h->n_dyn;
         p.key0 = (uint32_t)(h->seed & 0xffffffffu);
         p.key1 = (uint32_t)(h->seed >> 32);
         HASE_CUDA(h, launch_step(p, (uint32_t)h->groups.size(), h->threads, h->smem, st));
@@ -441,7 +501,7 @@ hase_status hase_set_state(hase_handle* h, const void* buf, size_t size, void* s
         for (uint32_t a = 0; a < E.n_agents; ++a) {
             uint16_t q;
             memcpy(&q, p + 2 * ((size_t)E.agent_off + a), 2);
-            if ((q & 0xffu) >= E.side || (q >> 8) >= E.side)
+            if (q >= 4096u || px(q) >= E.side || py(q) >= E.side)
                 return fail(h, HASE_EINVAL, "state blob: agent %u of env %u off the grid", a, e);
         }
     }
@@ -471,8 +531,8 @@ hase_status hase_get_world(hase_handle* h, uint32_t e, uint8_t* grid, int32_t* s
         std::vector<uint16_t> st(E.n_agents);
         HASE_CUDA(h, cudaMemcpy(st.data(), h->d_start + E.agent_off, 2 * st.size(), cudaMemcpyDeviceToHost));
         for (int a = 0; a < E.n_agents; ++a) {
-            start_xy[2 * a] = st[a] & 0xff;
-            start_xy[2 * a + 1] = st[a] >> 8;
+            start_xy[2 * a] = (int32_t)px(st[a]);
+            start_xy[2 * a + 1] = (int32_t)py(st[a]);
         }
     }
     return HASE_OK;

@@ -2,16 +2,17 @@
 // the batched hide-and-seek environment step (Hide-And-Seek-Engine, arxiv
 // 2604.27162).
 //
-// HBM layout of one handle (all device arrays, structure of arrays):
+// HBM layout of one handle (device arrays, structure of arrays):
 //   EnvRT    env[E]        per-env constants (32 B each)
 //   EnvState est[E]        episode counters
-//   uint16   pos[sumA]     current cell of every agent, x | y << 8
+//   uint16   pos[sumA]     current cell of every agent, packed x | y << 6
 //   uint16   start[sumA]   pristine start cells (Sec. 4.2 template)
-//   uint64   rows[...]     per env (S + 8) padded obstacle rows of RW words:
+//   uint64   rows[...]     per env (S + 8) padded obstacle rows of rw words:
 //                          bit x + 4 of row y + 4 is cell (x, y); every bit
 //                          outside the grid is 1, so windows that leave the
 //                          grid read obstacles without bounds checks
-//   Group    groups[G]     the envs one CTA steps together
+//   Group    groups[G]     the envs one CTA steps together (through a
+//   uint32   env_list[E]   permutation of the env indices)
 //   outputs                ring of ring_steps slots (see hase.h)
 #pragma once
 
@@ -19,11 +20,20 @@
 
 namespace hase {
 
-constexpr int kPad = 4;          // padding cells around the grid (max radius)
-constexpr int kMaxSlots = 16;    // agents per CTA group (half a warp)
-constexpr int kMaxGroupEnvs = 16;
-constexpr int kMaxChunk = 32;    // steps per on-chip chunk
-constexpr int kObsHiders = 2;    // obs_teams value: only hiders emit
+constexpr int kPad = 4;               // padding cells around the grid (max radius)
+constexpr int kMaxAgents = 16;        // agents per env
+constexpr int kMaxGroupEnvs = 64;     // envs per CTA
+constexpr int kMaxGroupSlots = 128;   // agents per CTA (four dynamics warps)
+constexpr int kMaxDyn = 4;            // dynamics warps per CTA
+constexpr int kMaxChunk = 32;         // steps per on-chip chunk
+constexpr int kObsHiders = 2;         // obs_teams value: only hiders emit
+constexpr uint32_t kDoneBit = 0x8000u;
+constexpr uint32_t kOccBit = 0x80u;   // occupancy bit of the neighbour map
+constexpr uint32_t kSmemBudget = 216 * 1024;  // dynamic shared memory per CTA
+
+__host__ __device__ inline uint32_t pack_xy(uint32_t x, uint32_t y) { return x | (y << 6); }
+__host__ __device__ inline uint32_t px(uint32_t p) { return p & 63u; }
+__host__ __device__ inline uint32_t py(uint32_t p) { return (p >> 6) & 63u; }
 
 struct EnvRT {
     uint8_t side, n_agents, n_seekers, r_seek;
@@ -42,28 +52,96 @@ struct EnvState {
     uint32_t ep_idx;  // finished episodes
 };
 
-struct Group {
-    uint32_t env_first;  // first env (envs of a group are consecutive)
-    uint16_t n_envs;
-    uint16_t n_slots;    // total agents of the group (<= kMaxSlots)
-};
+// Group flags.
+constexpr uint16_t kUseTable = 1;   // obstacle plane from per-cell window tables
 
-// Dynamic shared memory layout of one CTA (offsets in bytes from the base).
-struct SmemLayout {
-    uint32_t rows, nbr, act, traj, total;
+// All envs of a group share the radii, the emitting teams, the row width and
+// the agent and seeker counts, so one code path serves the whole CTA.
+struct Group {
+    uint32_t list_first;  // first entry in env_list
+    uint16_t n_envs;
+    uint16_t n_slots;
+    uint16_t flags;
+    uint8_t n_dyn;        // dynamics warps (whole envs of <= 32 agents each)
+    uint8_t pad;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+__host__ __device__ inline bool team_emits(const EnvRT& E, int team) { return (E.obs_teams >> team) & 1u; }
+__host__ __device__ inline int team_radius(const EnvRT& E, int team) { return team ? E.r_hide : E.r_seek; }
+__host__ __device__ inline uint32_t words_of_radius(int r) {
+    return (uint32_t)(((2 * r + 1) * (2 * r + 1) + 63) / 64);
+}
 
-// rows_words: padded row words of the group; nbr_bytes: sum of S*S.
-__host__ __device__ inline SmemLayout smem_layout(uint32_t rows_words, uint32_t nbr_bytes) {
-    SmemLayout L;
-    L.act = 0;                                         // uint8 [3][16][kMaxChunk]
-    L.traj = L.act + 3 * kMaxSlots * kMaxChunk;        // uint16 [2][kMaxChunk][16]
-    L.rows = align_up(L.traj + 2 * kMaxChunk * kMaxSlots * 2, 16);  // uint64
-    L.nbr = L.rows + rows_words * 8;                   // uint8
-    L.total = align_up(L.nbr + nbr_bytes, 16);
-    return L;
+// Inside a CTA a cell is packed as x | y << sh with sh = 5 for grids up to
+// 32 wide and 6 above; the per-env cell arrays are indexed by that value.
+__host__ __device__ inline uint32_t cell_shift(const EnvRT& E) { return E.side <= 32 ? 5u : 6u; }
+
+// Shared-memory plan of one CTA, computed identically on the host (to size
+// the launch) and on the device (to place the buffers).
+struct GroupPlan {
+    uint32_t rows_off[kMaxGroupEnvs];    // uint64 units (padded obstacle rows)
+    uint32_t cell_off[kMaxGroupEnvs];    // cells (2^sh * side per env): claim word + state byte
+    uint32_t tbl_off[kMaxGroupEnvs][2];  // uint64 units per team, ~0u = none
+    uint8_t first_slot[kMaxGroupEnvs];
+    uint8_t dyn_first[kMaxDyn + 1];      // slot range of every dynamics warp
+    uint32_t n_dyn;
+    uint32_t n_envs;
+    uint32_t n_slots;
+    uint32_t act_words;                  // uint32 words per action buffer
+    uint32_t act, traj, rows, claim, tbl, state, total;  // byte offsets
+    uint16_t flags;
+};
+
+// envs: the group's env constants in slot order.  Returns false when the
+// group does not fit the dynamics warps.
+__host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uint16_t flags,
+                                           GroupPlan& G) {
+    uint32_t ro = 0, co = 0, to = 0, slot = 0;
+    int dyn = 0;
+    uint32_t dyn_slots = 0;
+    G.dyn_first[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const EnvRT& E = envs[i];
+        if (dyn_slots + E.n_agents > 32u) {
+            if (dyn + 1 >= kMaxDyn) return false;
+            ++dyn;
+            G.dyn_first[dyn] = (uint8_t)slot;
+            dyn_slots = 0;
+        }
+        dyn_slots += E.n_agents;
+        G.first_slot[i] = (uint8_t)slot;
+        slot += E.n_agents;
+        G.rows_off[i] = ro;
+        ro += (uint32_t)(E.side + 2 * kPad) * E.rw;
+        G.cell_off[i] = co;
+        co += (1u << cell_shift(E)) * E.side;
+        for (int t = 0; t < 2; ++t) {
+            G.tbl_off[i][t] = ~0u;
+            if (!(flags & kUseTable) || !team_emits(E, t)) continue;
+            if (t == 1 && team_emits(E, 0) && E.r_hide == E.r_seek) {
+                G.tbl_off[i][1] = G.tbl_off[i][0];
+                continue;
+            }
+            G.tbl_off[i][t] = to;
+            to += (uint32_t)E.side * E.side * words_of_radius(team_radius(E, t));
+        }
+    }
+    G.n_dyn = (uint32_t)dyn + 1;
+    G.n_envs = (uint32_t)n;
+    G.n_slots = slot;
+    G.dyn_first[dyn + 1] = (uint8_t)slot;
+    const uint32_t ns = slot, kcu = (uint32_t)kc;
+    G.act_words = ((kcu + 3) / 4) * ns;                  // [kc/4][slots] words of 4 steps
+    G.act = 0;                                           // uint32 [3][act_words]
+    G.traj = align_up(G.act + 3 * G.act_words * 4, 16);  // uint16 [2][kc][slots]
+    G.rows = align_up(G.traj + 2 * kcu * ns * 2, 16);
+    G.claim = G.rows + ro * 8;                           // uint32 per cell
+    G.tbl = align_up(G.claim + co * 4, 16);
+    G.state = G.tbl + to * 8;                            // uint8 per cell
+    G.total = align_up(G.state + co, 16);
+    G.flags = flags;
+    return true;
 }
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
@@ -99,6 +177,7 @@ struct StepParams {
     const uint16_t* start;
     const uint64_t* rows;
     const Group* groups;
+    const uint32_t* env_list;
     uint64_t* obs;       // ring [ring][obs_words]
     int32_t* rew;        // ring [ring][agents]
     uint8_t* done;       // ring [ring][n_envs]
@@ -112,7 +191,8 @@ struct StepParams {
     uint32_t ring;
     uint32_t slot0;      // t0 mod ring
     uint32_t n_steps;
-    uint32_t kc;         // steps per chunk (<= kMaxChunk)
+    uint32_t kc;         // steps per chunk (<= kMaxChunk, <= ring)
+    uint32_t n_dyn;      // dynamics warps per CTA (the largest group's)
     uint32_t emit_warps;
     uint32_t key0, key1;
 };

@@ -18,8 +18,8 @@
 //                       reward with a warp ballot, write all outputs, and
 //                       draw the Philox actions of the next chunk (a1, a5,
 //                       a6, a9).
-//                   The sequential part (positions) is thus decoupled from
-//                   the bulk of the arithmetic and memory traffic, which is
+//                   The sequential part (positions) is decoupled from the
+//                   bulk of the arithmetic and memory traffic, which is
 //                   parallel over steps.
 #include <cuda_runtime.h>
 
@@ -34,63 +34,75 @@ namespace hase {
 // floor(u * n / 2^32)
 __device__ __forceinline__ uint32_t mulhi_n(uint32_t u, uint32_t n) { return __umulhi(u, n); }
 
-// D consecutive bits of a padded row starting at bit `start`.
-__device__ __forceinline__ uint32_t row_bits(const uint64_t* row, int rw, int start, uint32_t mask) {
-    if (rw == 1) return (uint32_t)(row[0] >> start) & mask;
+// D consecutive bits (mask) of a padded row of rw words starting at bit s.
+__device__ __forceinline__ uint32_t row_bits(const uint64_t* row, int rw, int s, uint32_t mask) {
+    if (rw == 1) return (uint32_t)(row[0] >> s) & mask;
     const uint64_t lo = row[0], hi = row[1];
     uint64_t v;
-    if (start >= 64)
-        v = hi >> (start - 64);
-    else if (start == 0)
+    if (s >= 64)
+        v = hi >> (s - 64);
+    else if (s == 0)
         v = lo;
     else
-        v = (lo >> start) | (hi << (64 - start));
+        v = (lo >> s) | (hi << (64 - s));
     return (uint32_t)v & mask;
 }
 
-// OR a short bit string v into the two-word plane (lo, hi) at bit sh.
+// OR a short bit string v (at most 9 bits) into the two-word plane (lo, hi)
+// at bit sh.
 __device__ __forceinline__ void or_bits(uint64_t& lo, uint64_t& hi, uint64_t v, int sh) {
     if (sh < 64) {
         lo |= v << sh;
-        if (sh > 0) hi |= v >> (64 - sh);
+        if (sh > 55) hi |= v >> (64 - sh);
     } else {
         hi |= v << (sh - 64);
     }
 }
 
-__device__ __forceinline__ int delta_of(uint32_t a) {
-    // 1 N: y - 1, 2 S: y + 1, 3 E: x + 1, 4 W: x - 1 (cells packed x | y << 8)
-    return a == 1u ? -256 : a == 2u ? 256 : a == 3u ? 1 : a == 4u ? -1 : 0;
+__device__ __forceinline__ void set_bit(uint64_t& lo, uint64_t& hi, int bit) {
+    if (bit < 64)
+        lo |= 1ull << bit;
+    else
+        hi |= 1ull << (bit - 64);
 }
 
-// Three observation planes (a5) of agent a of one env at (x, y) with radius
-// r, from the env's padded obstacle rows and the packed positions P[0..A).
-__device__ __forceinline__ void encode_planes(const uint64_t* rows, int rw, int x, int y, int r,
-                                              int a, int A, int ns, const uint16_t* P,
-                                              uint64_t pl[3][2]) {
+// packed-cell displacement of action a (x | y << 6): 1 N y-1, 2 S y+1,
+// 3 E x+1, 4 W x-1, 0 stay
+__device__ __forceinline__ int delta_of(uint32_t a) {
+    return a == 1u ? -64 : a == 2u ? 64 : a == 3u ? 1 : a == 4u ? -1 : 0;
+}
+
+// Obstacle plane (plane 0) of a window of radius r centred on (x, y) from
+// padded rows (rows point at padded row 0 of the env).
+__device__ __forceinline__ void obstacle_plane(const uint64_t* rows, int rw, int x, int y, int r,
+                                               uint64_t& lo, uint64_t& hi) {
     const int D = 2 * r + 1;
     const uint32_t mask = (1u << D) - 1u;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) pl[q][0] = pl[q][1] = 0;
-    const int xs = x - r + kPad;
+    const int s = x - r + kPad;
     const uint64_t* row = rows + (y - r + kPad) * rw;
-    for (int dy = 0; dy < D; ++dy) {
-        const uint32_t b = row_bits(row + dy * rw, rw, xs, mask);
-        or_bits(pl[0][0], pl[0][1], b, dy * D);
-    }
+    lo = hi = 0;
+    for (int dy = 0; dy < D; ++dy) or_bits(lo, hi, row_bits(row + dy * rw, rw, s, mask), dy * D);
+}
+
+// Ally / opponent planes of agent a from the packed positions P[0..A)
+// (pairwise; used for small groups and by the step -1 observation).
+__device__ __forceinline__ void team_planes_pairwise(int x, int y, int r, int a, int A, int ns,
+                                                     const uint16_t* P, uint64_t& al, uint64_t& ah,
+                                                     uint64_t& ol, uint64_t& oh) {
+    const int D = 2 * r + 1;
     const bool a_seek = a < ns;
+    al = ah = ol = oh = 0;
     for (int b = 0; b < A; ++b) {
         if (b == a) continue;
         const uint32_t q = P[b];
-        const int dx = (int)(q & 0xffu) - x + r;
-        const int dy = (int)((q >> 8) & 0x7fu) - y + r;
+        const int dx = (int)px(q) - x + r;
+        const int dy = (int)py(q) - y + r;
         if ((unsigned)dx < (unsigned)D && (unsigned)dy < (unsigned)D) {
             const int bit = dy * D + dx;
-            const int plane = ((b < ns) == a_seek) ? 1 : 2;
-            if (bit < 64)
-                pl[plane][0] |= 1ull << bit;
+            if ((b < ns) == a_seek)
+                set_bit(al, ah, bit);
             else
-                pl[plane][1] |= 1ull << (bit - 64);
+                set_bit(ol, oh, bit);
         }
     }
 }
@@ -99,9 +111,9 @@ __device__ __forceinline__ void encode_planes(const uint64_t* rows, int rw, int 
 // a0: generation.  One warp per env.
 // --------------------------------------------------------------------------
 __global__ void gen_kernel(const EnvRT* __restrict__ env, const uint32_t* __restrict__ thr,
-                           uint32_t n_envs, uint32_t key0,
-                           uint32_t key1, uint16_t* __restrict__ pos, uint16_t* __restrict__ start,
-                           uint64_t* __restrict__ rows, uint32_t* __restrict__ err) {
+                           uint32_t n_envs, uint32_t key0, uint32_t key1, uint16_t* __restrict__ pos,
+                           uint16_t* __restrict__ start, uint64_t* __restrict__ rows,
+                           uint32_t* __restrict__ err) {
     const uint32_t e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (e >= n_envs) return;
@@ -111,7 +123,7 @@ __global__ void gen_kernel(const EnvRT* __restrict__ env, const uint32_t* __rest
     // start cells: agent a draws word 0 of counter (attempt, a, env, 2),
     // redrawing while the cell is taken by an earlier agent.  Lane 0 alone.
     if (lane == 0) {
-        uint32_t mine[kMaxSlots];
+        uint32_t mine[kMaxAgents];
         for (int a = 0; a < A; ++a) {
             uint32_t attempt = 0, cell = 0;
             for (;;) {
@@ -127,7 +139,7 @@ __global__ void gen_kernel(const EnvRT* __restrict__ env, const uint32_t* __rest
                 }
             }
             mine[a] = cell;
-            const uint16_t p = (uint16_t)((cell % S) | ((cell / S) << 8));
+            const uint16_t p = (uint16_t)pack_xy(cell % S, cell / S);
             start[E.agent_off + a] = p;
             pos[E.agent_off + a] = p;
         }
@@ -148,13 +160,14 @@ __global__ void gen_kernel(const EnvRT* __restrict__ env, const uint32_t* __rest
                     blk = c >> 2;
                     uint32_t c0 = blk, c1 = 0u, c2 = E.env_id, c3 = 1u;
                     philox4x32_10(c0, c1, c2, c3, key0, key1);
-                    u[0] = c0; u[1] = c1; u[2] = c2; u[3] = c3;
+                    u[0] = c0;
+                    u[1] = c1;
+                    u[2] = c2;
+                    u[3] = c3;
                 }
                 bool blocked = u[c & 3u] < density_thr;
-                for (int a = 0; a < A; ++a) {
-                    const uint16_t p = start[E.agent_off + a];
-                    if ((p & 0xff) == x && (p >> 8) == y) blocked = false;
-                }
+                for (int a = 0; a < A; ++a)
+                    if (start[E.agent_off + a] == pack_xy(x, y)) blocked = false;
                 if (!blocked) {
                     const int bit = x + kPad;
                     if (bit < 64)
@@ -182,13 +195,14 @@ __global__ void observe_kernel(const EnvRT* __restrict__ env, uint32_t n_envs,
     const int a = threadIdx.x;
     if (a >= E.n_agents) return;
     const int ns = E.n_seekers;
-    const bool seek = a < ns;
-    if (!((E.obs_teams >> (seek ? 0 : 1)) & 1u)) return;
-    const int r = seek ? E.r_seek : E.r_hide;
+    const int team = a < ns ? 0 : 1;
+    if (!team_emits(E, team)) return;
+    const int r = team_radius(E, team);
     const uint32_t p = pos[E.agent_off + a];
     uint64_t pl[3][2];
-    encode_planes(rows + E.rows_off, E.rw, p & 0xff, p >> 8, r, a, E.n_agents, ns,
-                  pos + E.agent_off, pl);
+    obstacle_plane(rows + E.rows_off, E.rw, px(p), py(p), r, pl[0][0], pl[0][1]);
+    team_planes_pairwise(px(p), py(p), r, a, E.n_agents, ns, pos + E.agent_off, pl[1][0], pl[1][1],
+                         pl[2][0], pl[2][1]);
     const int ai = (E.obs_teams == kObsHiders) ? a - ns : a;
     const int W = E.wpp;
     uint64_t* o = obs + E.obs_off + (uint64_t)ai * 3 * W;
@@ -196,12 +210,11 @@ __global__ void observe_kernel(const EnvRT* __restrict__ env, uint32_t n_envs,
         for (int j = 0; j < W; ++j) o[q * W + j] = pl[q][j];
     if (unp) {
         const int D = 2 * r + 1;
-        // unpacked bytes of earlier emitting agents: same radius for a team
         uint8_t* u = unp + E.unp_off;
         for (int b = 0; b < a; ++b) {
-            const bool bs = b < ns;
-            if ((E.obs_teams >> (bs ? 0 : 1)) & 1u) {
-                const int rb = bs ? E.r_seek : E.r_hide;
+            const int tb = b < ns ? 0 : 1;
+            if (team_emits(E, tb)) {
+                const int rb = team_radius(E, tb);
                 u += 3 * (2 * rb + 1) * (2 * rb + 1);
             }
         }
@@ -213,270 +226,523 @@ __global__ void observe_kernel(const EnvRT* __restrict__ env, uint32_t n_envs,
 // --------------------------------------------------------------------------
 // a1-a9 fused over n_steps steps.
 // --------------------------------------------------------------------------
-struct CtaShared {
-    EnvRT env[kMaxGroupEnvs];
-    uint32_t rows_off[kMaxGroupEnvs];
-    uint32_t nbr_off[kMaxGroupEnvs];
-    uint32_t unp_rel[kMaxSlots];   // unpacked byte offset of the slot inside its env
-    uint16_t start[kMaxSlots];
-    uint16_t env_mask[kMaxSlots];  // slots (bits) sharing the env of slot s
-    uint8_t slot_env[kMaxSlots];
-    uint8_t slot_agent[kMaxSlots];
-    uint8_t first_slot[kMaxGroupEnvs];
-    uint32_t rows_total, nbr_total;
+struct SlotRec {
+    uint32_t obs_rel;  // first obs word of this agent inside a slot, ~0u if it emits none
+    uint32_t rew_rel;  // reward / action index inside a slot
+    uint32_t unp_rel;  // first unpacked byte inside a slot
+    uint16_t p0;       // pristine start cell (CTA packing x | y << sh)
+    uint8_t env;       // env index inside the group
+    uint8_t agent;     // agent index inside its env
 };
 
-__global__ void __launch_bounds__(512) step_kernel(const StepParams P) {
+struct CtaShared {
+    EnvRT env[kMaxGroupEnvs];
+    uint32_t gidx[kMaxGroupEnvs];  // handle env index (done byte, counters)
+    GroupPlan plan;
+    SlotRec slot[kMaxGroupSlots];
+    uint8_t team_list[2][kMaxGroupSlots];
+    uint32_t team_n[2];
+};
+
+__device__ __forceinline__ uint32_t to_cta(uint32_t p6, uint32_t sh) { return (p6 & 63u) | ((p6 >> 6) << sh); }
+__device__ __forceinline__ uint32_t to_hbm(uint32_t p, uint32_t sh) {
+    return (p & ((1u << sh) - 1u)) | ((p >> sh) << 6);
+}
+
+// action byte of (step k, slot s) in an action buffer of [kc/4][slots] words
+__device__ __forceinline__ uint32_t act_index(uint32_t k, uint32_t s, uint32_t nsl) {
+    return ((k >> 2) * nsl + s) * 4 + (k & 3);
+}
+
+// Context of one chunk's emission.
+struct EmitCtx {
+    const uint16_t* T;      // trajectory [kc][slots]
+    const uint8_t* act;     // action buffer of the chunk
+    const uint64_t* rows;   // padded obstacle rows
+    const uint64_t* tbl;    // obstacle-window tables
+    uint32_t len;           // steps in the chunk
+    uint32_t base_slot;     // ring slot of the chunk's first step
+    int worker, n_workers;  // this thread among the emission threads
+};
+
+// ---------------------------------------------------------------------------
+// Segment emission (a5, a6, a9): one thread handles all agents of one
+// (step, env) with the positions in registers.  For every ordered pair
+// (a, b) it tests b against a's window (radius of a's team); the bit goes to
+// a's plane of b's team.  When a is a seeker and b a hider the same test is
+// the reward's "seen" test (seeker radius).  The agent count A (<= 16) and
+// the seeker count are runtime values shared by the group; the loops are
+// unrolled to 16 and skip past A (warp-uniform).  NW = 32-bit words per
+// plane: 2 when every window fits 64 bits, 3 with radius 4.
+// ---------------------------------------------------------------------------
+template <int NW>
+struct Plane {
+    uint64_t lo;
+    uint32_t hi;  // bits 64.. (NW == 3)
+};
+
+template <int NW>
+__device__ __forceinline__ void plane_or(Plane<NW>& pl, bool in, uint32_t bit) {
+    if constexpr (NW == 2) {
+        pl.lo |= ((uint64_t)in) << (bit & 63u);  // bit < 64 whenever in
+    } else {
+        pl.lo |= ((uint64_t)(in && bit < 64u)) << (bit & 63u);
+        pl.hi |= (in && bit >= 64u) ? (1u << ((bit - 64u) & 31u)) : 0u;
+    }
+}
+
+// Lane-per-agent emission.  The lanes of one warp are cut into segments of
+// A lanes (A = agents per env, uniform in the group); a segment is one
+// (step, env) and lane a of it is agent a.  Every lane loads the env's A
+// positions (the same shared-memory words within a segment: broadcast),
+// tests the other agents against its own window, and the reward's "seen"
+// test is combined across the segment with warp ballots.
+template <int NW>
+__device__ __forceinline__ void emit_chunk(const StepParams& P, const CtaShared& H, const EmitCtx& C,
+                                           int ew, int M, int lane) {
+    constexpr int AM = kMaxAgents;
+    const GroupPlan& L = H.plan;
+    const uint32_t nsl = L.n_slots, ne = L.n_envs;
+    const EnvRT& E0 = H.env[0];
+    const int A = E0.n_agents, ns = E0.n_seekers;  // uniform in the group
+    const int segs = 32 / A;
+    const int seg = lane / A, a = lane - seg * A;
+    const bool seg_lane = seg < segs;
+    const uint32_t segmask = ((A == 32) ? 0xffffffffu : ((1u << A) - 1u)) << (seg_lane ? seg * A : 0);
+    const bool ta = a >= ns;
+    const int R = ta ? E0.r_hide : E0.r_seek;
+    const int D = 2 * R + 1;
+    const uint32_t twoR = (uint32_t)(2 * R);
+    const int rs = E0.r_seek;
+    const bool emits = team_emits(E0, ta ? 1 : 0);
+    const int ai = (E0.obs_teams == kObsHiders) ? a - ns : a;
+    const int W64 = E0.wpp;
+    const bool use_table = L.flags & kUseTable;
+    const uint32_t n_items = C.len * ne;
+    const uint32_t step_items = (uint32_t)(M * segs);
+    // this lane's first item and the stride of its (step, env) counters
+    uint32_t item = (uint32_t)(ew * segs + seg);
+    uint32_t k = item / ne, e = item % ne;
+    const uint32_t dk = step_items / ne, de = step_items % ne;
+    for (uint32_t base = (uint32_t)(ew * segs); base < n_items; base += step_items) {
+        const bool valid = seg_lane && item < n_items;
+        const uint32_t kk = valid ? k : 0u, ee = valid ? e : 0u;
+        const int first = L.first_slot[ee];
+        const uint32_t sh = cell_shift(H.env[ee]), xmask = (1u << sh) - 1u;
+        const uint16_t* Tk = C.T + kk * nsl + first;
+        const bool done = (Tk[0] & kDoneBit) != 0u;
+        int x[AM], y[AM];
+        uint32_t myseen = 0;  // seeker lanes: hiders b seen by this seeker
+        if (done) {
+            // the reward's "seen" test on the pre-reset positions
+            const uint32_t pa = Tk[a] & 0x0fffu;
+            const int xa = (int)(pa & xmask), ya = (int)(pa >> sh);
+#pragma unroll
+            for (int b = 0; b < AM; ++b) {
+                if (b >= A) break;
+                const uint32_t v = Tk[b] & 0x0fffu;
+                const int dx = abs((int)(v & xmask) - xa), dy = abs((int)(v >> sh) - ya);
+                if (!ta && b >= ns) myseen |= (uint32_t)(max(dx, dy) <= rs) << b;
+            }
+#pragma unroll
+            for (int b = 0; b < AM; ++b) {
+                if (b >= A) break;
+                const uint32_t p = H.slot[first + b].p0;
+                x[b] = (int)(p & xmask);
+                y[b] = (int)(p >> sh);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < AM; ++b) {
+                if (b >= A) break;
+                const uint32_t v = Tk[b];
+                x[b] = (int)(v & xmask);
+                y[b] = (int)((v & 0x0fffu) >> sh);
+            }
+        }
+        const uint32_t po = done ? (uint32_t)H.slot[first + a].p0 : (Tk[a] & 0x0fffu);
+        const int xo = (int)(po & xmask), yo = (int)(po >> sh);
+        const int xra = xo - R, yra = yo - R;
+        Plane<NW> ps, ph;  // bits of seekers / hiders in this agent's window
+        ps.lo = ph.lo = 0;
+        ps.hi = ph.hi = 0;
+#pragma unroll
+        for (int b = 0; b < AM; ++b) {
+            if (b >= A) break;
+            const uint32_t dx = (uint32_t)(x[b] - xra), dy = (uint32_t)(y[b] - yra);
+            const bool in = (max(dx, dy) <= twoR) && b != a;
+            const uint32_t bit = dy * (uint32_t)D + dx;
+            if (b < ns) {
+                plane_or<NW>(ps, in, bit);
+            } else {
+                plane_or<NW>(ph, in, bit);
+                if (!ta && !done) myseen |= (uint32_t)in << b;  // seeker window: radius rs
+            }
+        }
+        // a6: a hider is seen when some seeker of its segment sees it
+        uint32_t n_seen = 0;
+        bool me_seen = false;
+#pragma unroll
+        for (int h = 0; h < AM; ++h) {
+            if (h >= A) break;
+            if (h < ns) continue;
+            const uint32_t bal = __ballot_sync(0xffffffffu, valid && ((myseen >> h) & 1u));
+            const bool any = (bal & segmask) != 0u;
+            n_seen += any ? 1u : 0u;
+            me_seen |= any && h == a;
+        }
+        if (valid) {
+            uint32_t sl = C.base_slot + kk;
+            if (sl >= P.ring) sl -= P.ring;
+            const EnvRT& E = H.env[ee];
+            P.rew[(uint64_t)sl * P.agents + E.agent_off + a] = ta ? -(int32_t)me_seen : (int32_t)n_seen;
+            if (a == 0) P.done[(uint64_t)sl * P.n_envs + H.gidx[ee]] = done ? 3u : 0u;
+            if (P.act_out)
+                P.act_out[(uint64_t)sl * P.agents + E.agent_off + a] = C.act[act_index(kk, (uint32_t)(first + a), nsl)];
+            if (emits) {
+                // a5 obstacle plane
+                Plane<NW> o0;
+                if (use_table) {
+                    const uint32_t W = words_of_radius(R);
+                    const uint64_t* tw = C.tbl + L.tbl_off[ee][ta ? 1 : 0] + (uint32_t)(yo * E.side + xo) * W;
+                    o0.lo = tw[0];
+                    o0.hi = (NW == 3 && W == 2) ? (uint32_t)tw[1] : 0u;
+                } else {
+                    uint64_t lo, hi;
+                    obstacle_plane(C.rows + L.rows_off[ee], E.rw, xo, yo, R, lo, hi);
+                    o0.lo = lo;
+                    o0.hi = (uint32_t)hi;
+                }
+                const Plane<NW>& al = ta ? ph : ps;
+                const Plane<NW>& opp = ta ? ps : ph;
+                uint64_t* o = P.obs + (uint64_t)sl * P.obs_words + E.obs_off + (uint32_t)ai * 3u * (uint32_t)W64;
+                if (W64 == 1) {
+                    o[0] = o0.lo;
+                    o[1] = al.lo;
+                    o[2] = opp.lo;
+                } else {
+                    o[0] = o0.lo;
+                    o[1] = (uint64_t)o0.hi;
+                    o[2] = al.lo;
+                    o[3] = (uint64_t)al.hi;
+                    o[4] = opp.lo;
+                    o[5] = (uint64_t)opp.hi;
+                }
+                if (P.unp) {
+                    uint8_t* u = P.unp + (uint64_t)sl * P.unp_bytes + H.slot[first + a].unp_rel;
+                    const int DD = D * D;
+                    for (int q = 0; q < DD; ++q) {
+                        const uint32_t b0 = q < 64 ? (uint32_t)(o0.lo >> q) : (o0.hi >> (q - 64));
+                        const uint32_t b1 = q < 64 ? (uint32_t)(al.lo >> q) : (al.hi >> (q - 64));
+                        const uint32_t b2 = q < 64 ? (uint32_t)(opp.lo >> q) : (opp.hi >> (q - 64));
+                        u[q] = (uint8_t)(b0 & 1u);
+                        u[DD + q] = (uint8_t)(b1 & 1u);
+                        u[2 * DD + q] = (uint8_t)(b2 & 1u);
+                    }
+                }
+            }
+        }
+        item += step_items;
+        e += de;
+        k += dk;
+        if (e >= ne) {
+            e -= ne;
+            ++k;
+        }
+    }
+}
+
+// Per-cell shared state of the dynamics: a claim word (byte a-1 holds the
+// lane claiming the cell through action a, 1 N 2 S 3 E 4 W; 0xff = none)
+// and a state byte (bits 1..4: action a leads onto a free cell of the grid;
+// bit 7: occupied).
+constexpr uint32_t kNoClaims = 0xffffffffu;
+
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
     extern __shared__ __align__(16) uint8_t sm[];
     __shared__ CtaShared H;
     const Group G = P.groups[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthreads = blockDim.x;
     const int ne = G.n_envs, nsl = G.n_slots;
+    const int n_dyn = (int)P.n_dyn;  // dynamics warps of the launch (>= the group's)
+    const int M = (int)P.emit_warps;
+    const uint32_t kc = P.kc;
 
     if (tid == 0) {
-        uint32_t ro = 0, no = 0;
         int slot = 0;
+        H.team_n[0] = H.team_n[1] = 0;
         for (int i = 0; i < ne; ++i) {
-            const EnvRT E = P.env[G.env_first + i];
+            const uint32_t g = P.env_list[G.list_first + i];
+            const EnvRT E = P.env[g];
             H.env[i] = E;
-            H.rows_off[i] = ro;
-            ro += (uint32_t)(E.side + 2 * kPad) * E.rw;
-            H.nbr_off[i] = no;
-            no += (uint32_t)E.side * E.side;
-            H.first_slot[i] = (uint8_t)slot;
-            uint32_t urel = 0;
+            H.gidx[i] = g;
+            uint32_t urel = E.unp_off;
             for (int a = 0; a < E.n_agents; ++a) {
-                H.slot_env[slot] = (uint8_t)i;
-                H.slot_agent[slot] = (uint8_t)a;
-                H.unp_rel[slot] = urel;
-                const bool sk = a < E.n_seekers;
-                if ((E.obs_teams >> (sk ? 0 : 1)) & 1u) {
-                    const int r = sk ? E.r_seek : E.r_hide;
-                    urel += 3u * (2 * r + 1) * (2 * r + 1);
+                const int t = a < E.n_seekers ? 0 : 1;
+                SlotRec r;
+                r.env = (uint8_t)i;
+                r.agent = (uint8_t)a;
+                r.rew_rel = E.agent_off + a;
+                r.p0 = 0;
+                r.unp_rel = urel;
+                if (team_emits(E, t)) {
+                    const int ai = (E.obs_teams == kObsHiders) ? a - E.n_seekers : a;
+                    r.obs_rel = E.obs_off + (uint32_t)ai * 3u * E.wpp;
+                    const int rr = team_radius(E, t);
+                    urel += 3u * (2 * rr + 1) * (2 * rr + 1);
+                } else {
+                    r.obs_rel = ~0u;
                 }
+                H.slot[slot] = r;
+                H.team_list[t][H.team_n[t]++] = (uint8_t)slot;
                 ++slot;
             }
-            const uint16_t m = (uint16_t)(((1u << E.n_agents) - 1u) << H.first_slot[i]);
-            for (int a = 0; a < E.n_agents; ++a) H.env_mask[H.first_slot[i] + a] = m;
         }
-        H.rows_total = ro;
-        H.nbr_total = no;
+        plan_group(H.env, ne, (int)kc, G.flags, H.plan);
     }
     __syncthreads();
-    const SmemLayout L = smem_layout(H.rows_total, H.nbr_total);
-    uint8_t* s_act = sm + L.act;                         // [3][16][kMaxChunk]
-    uint16_t* s_traj = (uint16_t*)(sm + L.traj);         // [2][kMaxChunk][16]
+    const GroupPlan& L = H.plan;
+    const bool use_table = L.flags & kUseTable;
+    uint8_t* s_act = sm + L.act;                     // [3][act_words] (bytes of 4 steps)
+    uint16_t* s_traj = (uint16_t*)(sm + L.traj);     // [2][kc][slots]
     uint64_t* s_rows = (uint64_t*)(sm + L.rows);
-    uint8_t* s_nbr = sm + L.nbr;
+    uint32_t* s_claim = (uint32_t*)(sm + L.claim);   // per cell
+    uint8_t* s_state = sm + L.state;                 // per cell
+    uint64_t* s_tbl = (uint64_t*)(sm + L.tbl);
+    const uint32_t act_bytes = L.act_words * 4;
 
     // stage the pristine template: padded rows and start cells
     for (int i = 0; i < ne; ++i) {
         const EnvRT& E = H.env[i];
         const uint32_t n = (uint32_t)(E.side + 2 * kPad) * E.rw;
-        for (uint32_t j = tid; j < n; j += nthreads) s_rows[H.rows_off[i] + j] = P.rows[E.rows_off + j];
+        for (uint32_t j = tid; j < n; j += nthreads) s_rows[L.rows_off[i] + j] = P.rows[E.rows_off + j];
     }
-    if (tid < nsl) {
-        const EnvRT& E = H.env[H.slot_env[tid]];
-        H.start[tid] = P.start[E.agent_off + H.slot_agent[tid]];
+    for (int sidx = tid; sidx < nsl; sidx += nthreads) {
+        const SlotRec& r = H.slot[sidx];
+        const EnvRT& E = H.env[r.env];
+        H.slot[sidx].p0 = (uint16_t)to_cta(P.start[E.agent_off + r.agent], cell_shift(E));
     }
     __syncthreads();
-    // passable-neighbour masks: bit a set iff action a (1 N, 2 S, 3 E, 4 W)
-    // leads onto a free cell inside the grid
+    // cell state and claims, obstacle-window tables (plane 0 of every cell
+    // for each emitting radius)
     for (int i = 0; i < ne; ++i) {
         const EnvRT& E = H.env[i];
         const int S = E.side, rw = E.rw;
-        const uint64_t* R = s_rows + H.rows_off[i];
-        for (int c = tid; c < S * S; c += nthreads) {
-            const int x = c % S, y = c / S;
-            auto blocked = [&](int xx, int yy) -> uint32_t {
-                const int b = xx + kPad;
-                return (uint32_t)((R[(yy + kPad) * rw + (b >> 6)] >> (b & 63)) & 1ull);
-            };
-            const uint32_t m = ((blocked(x, y - 1) ^ 1u) << 1) | ((blocked(x, y + 1) ^ 1u) << 2) |
-                               ((blocked(x + 1, y) ^ 1u) << 3) | ((blocked(x - 1, y) ^ 1u) << 4);
-            s_nbr[H.nbr_off[i] + c] = (uint8_t)m;
+        const uint32_t sh = cell_shift(E);
+        const uint64_t* Rw = s_rows + L.rows_off[i];
+        for (int c = tid; c < (S << sh); c += nthreads) {
+            const int x = c & ((1 << sh) - 1), y = c >> sh;
+            uint32_t m = 0;
+            if (x < S) {
+                auto freecell = [&](int xx, int yy) -> uint32_t {
+                    const int b = xx + kPad;
+                    return (uint32_t)(((Rw[(yy + kPad) * rw + (b >> 6)] >> (b & 63)) & 1ull) ^ 1ull);
+                };
+                m = (freecell(x, y - 1) << 1) | (freecell(x, y + 1) << 2) | (freecell(x + 1, y) << 3) |
+                    (freecell(x - 1, y) << 4);
+            }
+            s_state[L.cell_off[i] + c] = (uint8_t)m;
+            s_claim[L.cell_off[i] + c] = kNoClaims;
+        }
+        if (use_table) {
+            for (int t = 0; t < 2; ++t) {
+                if (L.tbl_off[i][t] == ~0u) continue;
+                if (t == 1 && L.tbl_off[i][1] == L.tbl_off[i][0]) continue;
+                const int r = team_radius(E, t);
+                const uint32_t W = words_of_radius(r);
+                uint64_t* Tb = s_tbl + L.tbl_off[i][t];
+                for (int c = tid; c < S * S; c += nthreads) {
+                    uint64_t lo, hi;
+                    obstacle_plane(Rw, rw, c % S, c / S, r, lo, hi);
+                    Tb[c * W] = lo;
+                    if (W == 2) Tb[c * W + 1] = hi;
+                }
+            }
         }
     }
+    __syncthreads();
+    // occupancy bits of the current cells
+    for (int sidx = tid; sidx < nsl; sidx += nthreads) {
+        const SlotRec& r = H.slot[sidx];
+        const EnvRT& E = H.env[r.env];
+        const uint32_t p = to_cta(P.pos[E.agent_off + r.agent], cell_shift(E));
+        s_state[L.cell_off[r.env] + p] |= (uint8_t)kOccBit;
+    }
 
-    const uint32_t kc = P.kc;
     const uint32_t n_chunks = (P.n_steps + kc - 1) / kc;
-    const int M = P.emit_warps;
 
-    // a1: Philox actions of chunk c into buffer c % 3.  Items (block, slot);
-    // one Philox block serves four consecutive steps.
+    // a1: Philox actions of chunk c into buffer c % 3.  Worker w serves slot
+    // w % nsl and every (n_workers / nsl)-th Philox block; one block serves
+    // four consecutive steps.
     auto draw_actions = [&](uint32_t c, int worker, int n_workers) {
         const uint64_t ts = P.t0 + (uint64_t)c * kc;
         const uint32_t len = min(kc, P.n_steps - c * kc);
         const uint64_t te = ts + len;
-        const uint64_t b0 = ts >> 2, b1 = (te - 1) >> 2;
-        const uint32_t nblk = (uint32_t)(b1 - b0 + 1);
-        uint8_t* A = s_act + (c % 3u) * (kMaxSlots * kMaxChunk);
-        for (uint32_t it = worker; it < nblk * (uint32_t)nsl; it += n_workers) {
-            const uint32_t bi = it / nsl, s = it % nsl;
-            const EnvRT& E = H.env[H.slot_env[s]];
-            uint32_t c0 = (uint32_t)(b0 + bi), c1 = H.slot_agent[s], c2 = E.env_id, c3 = 0u;
-            philox4x32_10(c0, c1, c2, c3, P.key0, P.key1);
-            const uint32_t u[4] = {c0, c1, c2, c3};
+        const uint64_t b0 = ts >> 2;
+        const uint32_t nblk = (uint32_t)(((te - 1) >> 2) - b0 + 1);
+        uint8_t* A = s_act + (c % 3u) * act_bytes;
+        const int per = max(1, n_workers / nsl);
+        const int s_first = worker % nsl, sub = worker / nsl;
+        if (n_workers >= nsl && sub >= per) return;
+        for (int s = s_first; s < nsl; s += (n_workers >= nsl ? nsl : n_workers)) {
+            const SlotRec& r = H.slot[s];
+            const uint32_t agent = r.agent;
+            const uint32_t env_id = H.env[r.env].env_id;
+            for (uint32_t bi = (n_workers >= nsl ? sub : 0); bi < nblk; bi += per) {
+                uint32_t c0 = (uint32_t)(b0 + bi), c1 = agent, c2 = env_id, c3 = 0u;
+                philox4x32_10(c0, c1, c2, c3, P.key0, P.key1);
+                const uint32_t u[4] = {c0, c1, c2, c3};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint64_t t = (b0 + bi) * 4 + j;
-                if (t >= ts && t < te) A[s * kMaxChunk + (uint32_t)(t - ts)] = (uint8_t)mulhi_n(u[j], 5u);
+                for (int j = 0; j < 4; ++j) {
+                    const uint64_t t = (b0 + bi) * 4 + j;
+                    if (t >= ts && t < te) A[act_index((uint32_t)(t - ts), s, nsl)] = (uint8_t)mulhi_n(u[j], 5u);
+                }
             }
+            if (n_workers >= nsl) break;
         }
     };
 
     if (n_chunks > 0) draw_actions(0, tid, nthreads);
     __syncthreads();
 
-    // ---------------- dynamics warp state ----------------
-    const int s_dyn = lane & 15;
-    const bool up = lane >= 16;
-    const bool live = (warp == 0) && s_dyn < nsl;
-    uint32_t p = 0, p0 = 0, nbr_cur = 0, nbr0 = 0, ep_t = 0, ep_idx = 0, cap = 1;
-    uint32_t eb = 0, S_dyn = 1, lowmask = 0xffffffffu;
-    const uint8_t* nb = s_nbr;
-    int env_dyn = 0;
-    if (warp == 0) {
+    if (warp < n_dyn) {
+        // ================= dynamics warps: a2 a3 a7 a8 =================
+        // lane = agent slot; whole envs per warp, lanes in agent order.  A
+        // mover claims its target in the byte of its incoming direction;
+        // after a __syncwarp it reads the target's claim word and state: it
+        // moves iff the target was unoccupied and no lower lane claimed it.
+        // Episode ends are known in advance (truncation only), so the reset
+        // path is a warp-uniform branch taken once per episode.
+        const int d_first = warp < (int)L.n_dyn ? L.dyn_first[warp] : 0;
+        const int d_end = warp < (int)L.n_dyn ? L.dyn_first[warp + 1] : 0;
+        const int s = d_first + lane;
+        const bool live = s < d_end;
+        uint32_t p = 0, p0 = 0, nbr_cur = 0, nbr0 = 0, ep_idx = 0, cap = 1, sh = 5;
+        uint32_t next_done = 0xffffffffu;  // launch step index of this lane's next episode end
+        int env = 0;
+        uint8_t* st8 = s_state;
+        uint8_t* cl8 = reinterpret_cast<uint8_t*>(s_claim);
         if (live) {
-            env_dyn = H.slot_env[s_dyn];
-            const EnvRT& E = H.env[env_dyn];
-            S_dyn = E.side;
-            nb = s_nbr + H.nbr_off[env_dyn];
-            p = P.pos[E.agent_off + H.slot_agent[s_dyn]];
-            p0 = H.start[s_dyn];
-            nbr_cur = nb[(p >> 8) * S_dyn + (p & 0xff)];
-            nbr0 = nb[(p0 >> 8) * S_dyn + (p0 & 0xff)];
-            const EnvState st = P.est[G.env_first + env_dyn];
-            ep_t = st.ep_t;
-            ep_idx = st.ep_idx;
+            const SlotRec& r = H.slot[s];
+            env = r.env;
+            const EnvRT& E = H.env[env];
+            sh = cell_shift(E);
+            st8 = s_state + L.cell_off[env];
+            cl8 = reinterpret_cast<uint8_t*>(s_claim + L.cell_off[env]);
+            p = to_cta(P.pos[E.agent_off + r.agent], sh);
+            p0 = r.p0;
+            nbr_cur = st8[p] & 0x1eu;
+            nbr0 = st8[p0] & 0x1eu;
+            const EnvState est = P.est[H.gidx[env]];
+            ep_idx = est.ep_idx;
             cap = E.cap;
-            eb = (uint32_t)env_dyn << 16;
+            next_done = cap - 1u - est.ep_t;
         }
-        if (up) lowmask = 0xffffu | (((1u << s_dyn) - 1u) << 16);
-    }
-    const uint32_t sent = 0x80000000u | (uint32_t)lane;
-
-    // ---------------- emission lane mapping ----------------
-    const int ew = warp - 1;                   // emission warp index
-    const int segs = 32 / nsl;                 // (step, group) segments per warp
-    const int seg = lane / nsl;
-    const int s_em = lane - seg * nsl;
-    const bool em_lane = seg < segs;
-
-    for (uint32_t c = 0; c <= n_chunks; ++c) {
-        if (warp == 0) {
+        uint32_t warp_next = __reduce_min_sync(0xffffffffu, next_done);
+        const uint32_t lane_rep = 0x01010101u * (uint32_t)lane;
+        // byte a-1: displacement of action a (1 N, 2 S, 3 E, 4 W) plus 64
+        const uint32_t dn = 1u << sh;
+        const uint32_t dlut = (64u - dn) | ((64u + dn) << 8) | (65u << 16) | (63u << 24);
+        __syncwarp();
+        // One step: claim, read, resolve, update.  g: step inside the launch.
+        auto step = [&](uint32_t a, uint16_t* Tk, uint32_t g) {
+            const uint32_t dd = __byte_perm(dlut, 0, 0x4440u | ((a + 3u) & 3u)) - 64u;
+            const uint32_t tgt = p + dd;
+            const uint32_t open = (nbr_cur >> a) & 1u;  // inside the grid, no obstacle (a = 0: never)
+            if (open) cl8[tgt * 4 + a - 1] = (uint8_t)lane;  // claim the byte of direction a
+            __syncwarp();
+            uint32_t claims = 0u, tst = kOccBit;         // not open: reads as occupied
+            if (open) {
+                claims = *reinterpret_cast<const uint32_t*>(cl8 + tgt * 4);
+                tst = st8[tgt];
+            }
+            const uint32_t lower = ~((claims | 0x80808080u) - lane_rep) & 0x80808080u;
+            const bool won = ((tst & kOccBit) | lower) == 0u;
+            __syncwarp();  // every read of this step is done
+            if (open) cl8[tgt * 4 + a - 1] = 0xffu;          // release the claim
+            if (won) {
+                st8[p] = (uint8_t)nbr_cur;
+                st8[tgt] = (uint8_t)(tst | kOccBit);
+            }
+            p = won ? tgt : p;
+            nbr_cur = won ? (tst & 0x1eu) : nbr_cur;
+            if (live) *Tk = (uint16_t)(p | (g == next_done ? kDoneBit : 0u));
+            if (g == warp_next) {  // some env of this warp ends its episode (a8)
+                const bool done = g == next_done;
+                __syncwarp();
+                if (done) st8[p] = (uint8_t)nbr_cur;
+                __syncwarp();
+                if (done) {
+                    st8[p0] = (uint8_t)(nbr0 | kOccBit);
+                    p = p0;
+                    nbr_cur = nbr0;
+                    next_done += cap;
+                    ++ep_idx;
+                }
+                warp_next = __reduce_min_sync(0xffffffffu, next_done);
+            }
+            __syncwarp();  // state writes visible to the next step
+        };
+        for (uint32_t c = 0; c <= n_chunks; ++c) {
             if (c < n_chunks) {
-                // ---------------- a2 a3 a7 a8: positions of chunk c ----------------
                 const uint32_t len = min(kc, P.n_steps - c * kc);
-                const uint8_t* A = s_act + (c % 3u) * (kMaxSlots * kMaxChunk) + s_dyn * kMaxChunk;
-                uint16_t* T = s_traj + (c & 1u) * (kMaxChunk * kMaxSlots);
-                for (uint32_t k = 0; k < len; ++k) {
-                    const uint32_t a = live ? A[k] : 0u;
-                    const uint32_t tgt = p + (uint32_t)delta_of(a);
-                    const bool valid = live && ((nbr_cur >> a) & 1u);
-                    uint32_t ntgt = 0;
-                    if (valid) ntgt = nb[(tgt >> 8) * S_dyn + (tgt & 0xff)];
-                    const uint32_t key = !live ? sent : (up ? (valid ? (eb | tgt) : sent) : (eb | p));
-                    const uint32_t m = __match_any_sync(0xffffffffu, key);
-                    const bool won = up && valid && ((m & lowmask) == 0u);
-                    const uint32_t bal = __ballot_sync(0xffffffffu, won);
-                    if ((bal >> (16 + s_dyn)) & 1u) {
-                        p = tgt;
-                        nbr_cur = ntgt;
-                    }
-                    ++ep_t;
-                    const bool done = ep_t == cap;
-                    if (live && !up) T[k * kMaxSlots + s_dyn] = (uint16_t)(p | (done ? 0x8000u : 0u));
-                    if (done) {
-                        p = p0;
-                        nbr_cur = nbr0;
-                        ep_t = 0;
-                        ++ep_idx;
-                    }
+                const uint32_t* A = reinterpret_cast<const uint32_t*>(s_act + (c % 3u) * act_bytes) + s;
+                uint16_t* T = s_traj + (c & 1u) * (kc * nsl) + s;
+                const uint32_t g0 = c * kc;
+                uint32_t k = 0;
+                uint32_t aw = live ? A[0] : 0u;
+                for (; k + 4 <= len; k += 4) {
+                    const uint32_t aw_next = (live && k + 4 < len) ? A[((k + 4) >> 2) * nsl] : 0u;
+#pragma unroll
+                    for (uint32_t j = 0; j < 4; ++j)
+                        step(__byte_perm(aw, 0, 0x4440u + j), T + (k + j) * nsl, g0 + k + j);
+                    aw = aw_next;
                 }
+                for (; k < len; ++k) step(__byte_perm(aw, 0, 0x4440u + (k & 3u)), T + k * nsl, g0 + k);
             }
-        } else {
-          if (c >= 1) {
-            // ---------------- a5 a6 a9: outputs of chunk c - 1 ----------------
-            const uint32_t cp = c - 1;
-            const uint32_t len = min(kc, P.n_steps - cp * kc);
-            const uint16_t* T = s_traj + (cp & 1u) * (kMaxChunk * kMaxSlots);
-            const uint8_t* Aact = s_act + (cp % 3u) * (kMaxSlots * kMaxChunk);
-            // ring slot of the chunk's first step
-            const uint32_t base_slot = (uint32_t)(((uint64_t)P.slot0 + (uint64_t)cp * kc) % P.ring);
-            const int ei = em_lane ? H.slot_env[s_em] : 0;
-            const EnvRT& E = H.env[ei];
-            const int a = em_lane ? H.slot_agent[s_em] : 0;
-            const int ns = E.n_seekers, An = E.n_agents;
-            const bool seek = a < ns;
-            const bool emits = em_lane && ((E.obs_teams >> (seek ? 0 : 1)) & 1u);
-            const int r = seek ? E.r_seek : E.r_hide;
-            const int W = E.wpp;
-            const int ai = (E.obs_teams == kObsHiders) ? a - ns : a;
-            const int first = H.first_slot[ei];
-            const uint32_t envmask = em_lane ? ((uint32_t)H.env_mask[s_em] << (seg * nsl)) : 0u;
-            const uint32_t rs = E.r_seek;
-            for (uint32_t kb = (uint32_t)(ew * segs); kb < len; kb += (uint32_t)(M * segs)) {
-                const uint32_t k = kb + (uint32_t)seg;
-                const bool act_item = em_lane && k < len;
-                const uint16_t* Tk = T + (act_item ? k : 0) * kMaxSlots;
-                const uint32_t v = Tk[s_em];
-                const bool done = (v >> 15) & 1u;
-                // a6: hider seen by a seeker (post-move, pre-reset positions)
-                bool seen = false;
-                if (act_item && !seek) {
-                    const int hx = v & 0xff, hy = (v >> 8) & 0x7f;
-                    for (int j = 0; j < ns; ++j) {
-                        const uint32_t q = Tk[first + j];
-                        const int dx = abs((int)(q & 0xff) - hx), dy = abs((int)((q >> 8) & 0x7f) - hy);
-                        seen |= max(dx, dy) <= (int)rs;
-                    }
-                }
-                const uint32_t bal = __ballot_sync(0xffffffffu, seen);
-                if (!act_item) continue;
-                const int32_t reward = seek ? (int32_t)__popc(bal & envmask) : (seen ? -1 : 0);
-                uint32_t slot = base_slot + k;
-                while (slot >= P.ring) slot -= P.ring;
-                P.rew[(uint64_t)slot * P.agents + E.agent_off + a] = reward;
-                if (a == 0) P.done[(uint64_t)slot * P.n_envs + G.env_first + ei] = done ? 3u : 0u;
-                if (P.act_out) P.act_out[(uint64_t)slot * P.agents + E.agent_off + a] = Aact[s_em * kMaxChunk + k];
-                if (emits) {
-                    // a5 on the post-reset positions
-                    const uint16_t* Pos = done ? (H.start + first) : (Tk + first);
-                    const uint32_t pp = Pos[a];
-                    uint64_t pl[3][2];
-                    encode_planes(s_rows + H.rows_off[ei], E.rw, pp & 0xff, (pp >> 8) & 0x7f, r, a, An,
-                                  ns, Pos, pl);
-                    uint64_t* o = P.obs + (uint64_t)slot * P.obs_words + E.obs_off + (uint64_t)ai * 3 * W;
-                    for (int q = 0; q < 3; ++q)
-                        for (int j = 0; j < W; ++j) o[q * W + j] = pl[q][j];
-                    if (P.unp) {
-                        const int D = 2 * r + 1;
-                        uint8_t* u = P.unp + (uint64_t)slot * P.unp_bytes + E.unp_off + H.unp_rel[s_em];
-                        for (int q = 0; q < 3; ++q)
-                            for (int kk = 0; kk < D * D; ++kk)
-                                u[q * D * D + kk] = (uint8_t)((pl[q][kk >> 6] >> (kk & 63)) & 1u);
-                    }
-                }
-            }
-          }
-          // a1 for chunk c + 1
-          if (c + 1 < n_chunks) draw_actions(c + 1, tid - 32, M * 32);
+            __syncthreads();
         }
-        __syncthreads();
+        // write back the dynamic state
+        if (live) {
+            const SlotRec& r = H.slot[s];
+            const EnvRT& E = H.env[env];
+            P.pos[E.agent_off + r.agent] = (uint16_t)to_hbm(p, sh);
+            if (r.agent == 0) {
+                EnvState est;
+                est.ep_t = cap - 1u - (next_done - P.n_steps);
+                est.ep_idx = ep_idx;
+                P.est[H.gidx[env]] = est;
+            }
+        }
+        return;
     }
 
-    // write back the dynamic state
-    if (warp == 0 && live && !up) {
-        const EnvRT& E = H.env[env_dyn];
-        P.pos[E.agent_off + H.slot_agent[s_dyn]] = (uint16_t)p;
-        if (H.slot_agent[s_dyn] == 0) {
-            EnvState st;
-            st.ep_t = ep_t;
-            st.ep_idx = ep_idx;
-            P.est[G.env_first + env_dyn] = st;
+    // ================= emission warps: a5 a6 a9 (+ a1 ahead) =================
+    const int worker = tid - n_dyn * 32;
+    const int n_workers = M * 32;
+    const bool wide = H.env[0].wpp == 2;  // the group shares its radii
+    for (uint32_t c = 0; c <= n_chunks; ++c) {
+        if (c >= 1) {
+            const uint32_t cp = c - 1;
+            EmitCtx C;
+            C.len = min(kc, P.n_steps - cp * kc);
+            C.T = s_traj + (cp & 1u) * (kc * nsl);
+            C.act = s_act + (cp % 3u) * act_bytes;
+            C.rows = s_rows;
+            C.tbl = s_tbl;
+            C.base_slot = (uint32_t)(((uint64_t)P.slot0 + (uint64_t)cp * kc) % P.ring);
+            C.worker = worker;
+            C.n_workers = n_workers;
+            if (wide)
+                emit_chunk<3>(P, H, C, warp - n_dyn, M, lane);
+            else
+                emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
         }
+        // a1 for chunk c + 1
+        if (c + 1 < n_chunks) draw_actions(c + 1, worker, n_workers);
+        __syncthreads();
     }
 }
 
@@ -500,16 +766,30 @@ cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* po
     return cudaGetLastError();
 }
 
+template <int MAXT, int MINB>
+static cudaError_t launch_step_t(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
+                                 cudaStream_t st) {
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<MAXT, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    step_kernel<MAXT, MINB><<<n_groups, threads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+// The register budget follows the CTA size: up to 128 registers a thread
+// (the emission thread keeps a whole env's positions in registers), so CTAs
+// of 64 / 96 / 128 threads keep 8 / 5 / 4 resident per SM when the groups
+// run in waves; the persistent one-CTA-per-SM shapes use up to 512 threads.
 cudaError_t launch_step(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
                         cudaStream_t st) {
     if (n_groups == 0 || p.n_steps == 0) return cudaSuccess;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    step_kernel<<<n_groups, threads, smem, st>>>(p);
-    return cudaGetLastError();
+    if (threads <= 64) return launch_step_t<64, 8>(p, n_groups, threads, smem, st);
+    if (threads <= 96) return launch_step_t<96, 5>(p, n_groups, threads, smem, st);
+    if (threads <= 128) return launch_step_t<128, 4>(p, n_groups, threads, smem, st);
+    if (threads <= 512) return launch_step_t<512, 1>(p, n_groups, threads, smem, st);
+    return cudaErrorInvalidConfiguration;
 }
 
 }  // namespace hase

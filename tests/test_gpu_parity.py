@@ -54,7 +54,7 @@ def test_uneven_batch():
     dict(chunk_steps=1, emit_warps=1),
     dict(chunk_steps=5, emit_warps=2, steps_per_launch=7),
     dict(chunk_steps=32, emit_warps=7, max_group_envs=1),
-    dict(chunk_steps=13, emit_warps=15, steps_per_launch=1),
+    dict(chunk_steps=13, emit_warps=12, steps_per_launch=1),
     dict(chunk_steps=4, emit_warps=4, max_group_envs=3),
 ])
 def test_launch_configurations_agree(tuning):
