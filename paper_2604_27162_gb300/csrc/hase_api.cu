@@ -275,12 +275,18 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
     if (n_sm <= 0) n_sm = 1;
     make_groups(h, cfg->max_group_envs, (uint32_t)n_sm);
-    // emission warps: enough to fill 16 warps per CTA in the persistent
-    // regime, a few per group when CTAs run in waves
-    if (cfg->emit_warps)
+    // emission warps.  Persistent regime (one CTA per SM): four when every
+    // group emits one (step, env) per thread (more warps only add store
+    // traffic in flight), else twelve; CTAs in waves: six.
+    if (cfg->emit_warps) {
         h->emit_warps = cfg->emit_warps;
-    else
-        h->emit_warps = h->groups.size() <= (size_t)n_sm ? 12u : 3u;
+    } else if (h->groups.size() <= (size_t)n_sm) {
+        bool fast = !(h->flags & HASE_EXPORT_UNPACKED);
+        for (const Group& g : h->groups) fast = fast && fast_emission(h->env[h->env_list[g.list_first]]);
+        h->emit_warps = fast ? 4u : 12u;
+    } else {
+        h->emit_warps = 6u;
+    }
     h->threads = 32 * (h->n_dyn + h->emit_warps);
 
     auto alloc = [&](void** p, size_t bytes) -> cudaError_t {

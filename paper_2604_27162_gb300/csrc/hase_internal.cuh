@@ -93,6 +93,12 @@ struct GroupPlan {
     uint16_t flags;
 };
 
+// One thread emits a whole (step, env) when every window fits one word and
+// the seekers are the first ceil(A / 2) agents.
+__host__ __device__ inline bool fast_emission(const EnvRT& E) {
+    return E.wpp == 1 && E.n_seekers == (E.n_agents + 1u) / 2u;
+}
+
 // envs: the group's env constants in slot order.  Returns false when the
 // group does not fit the dynamics warps.
 __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uint16_t flags,

@@ -240,6 +240,8 @@ struct CtaShared {
     uint32_t gidx[kMaxGroupEnvs];  // handle env index (done byte, counters)
     GroupPlan plan;
     SlotRec slot[kMaxGroupSlots];
+    uint16_t p0[kMaxGroupSlots];  // pristine start cells (CTA packing)
+    uint2 key[kMaxGroupSlots];     // Philox action counter words (agent, env id)
     uint8_t team_list[2][kMaxGroupSlots];
     uint32_t team_n[2];
 };
@@ -452,6 +454,245 @@ __device__ __forceinline__ void emit_chunk(const StepParams& P, const CtaShared&
     }
 }
 
+// Reward "seen" mask of a segment whose episode ended in this step: the test
+// runs on the pre-reset positions (one step in cap takes this path).
+__device__ __forceinline__ uint32_t seen_pre_reset(const uint16_t* Tk, int A, int ns, int rs, uint32_t sh) {
+    const uint32_t xmask = (1u << sh) - 1u;
+    uint32_t seen = 0;
+    for (int h = ns; h < A; ++h) {
+        const uint32_t vh = Tk[h] & 0x0fffu;
+        const int hx = (int)(vh & xmask), hy = (int)(vh >> sh);
+        for (int s = 0; s < ns; ++s) {
+            const uint32_t vs = Tk[s] & 0x0fffu;
+            const int dx = abs((int)(vs & xmask) - hx), dy = abs((int)(vs >> sh) - hy);
+            if (max(dx, dy) <= rs) seen |= 1u << h;
+        }
+    }
+    return seen;
+}
+
+// PTX shifts clamp the amount at the register width: 1 << n is 0 for n >= 32.
+__device__ __forceinline__ uint32_t shl_clamp(uint32_t v, uint32_t n) {
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(n));
+    return r;
+}
+
+// Byte q of w (q a compile-time constant after unrolling).
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int q) { return q == 3 ? w >> 24 : (w >> (8 * q)) & 0xffu; }
+
+// Segment emission with compile-time A (seekers NS = ceil(A/2)) and windows
+// of at most 64 bits (radius <= 3): one thread handles one (step, env), and
+// the window tests run four agents at a time on bytes packed in a word.
+//   X4 / Y4: byte b & 3 of word b >> 2 holds agent b's x / y;
+//   P4:      the same byte holds (y D + x) mod 256 for the team's D.
+// For observer a with radius R, adding (0x80 + R - x_a) to every byte of X4
+// gives dx + R + 0x80 in [0x41, 0xc3] (no carry leaves a byte); b lies in the
+// window iff both that byte and its y twin are in [0x80, 0x80 + 2R].  The
+// window bit (dy + R) D + (dx + R) equals P4_b - P4_a + R D + R mod 256 for
+// agents inside the window; a byte-wise add (carries kept inside each byte)
+// forms it, and bit 7 is set in the bytes of agents outside, which makes the
+// shifts below yield 0 for them (PTX clamps shift amounts at 32).  Observer a
+// meets itself at the window centre of its ally plane, cleared afterwards
+// (no other agent shares its cell).
+// Loop-invariant inputs of one team's observers in one (step, env).
+struct TeamCtx {
+    const uint16_t* src;  // observed positions (CTA packing), shared memory
+    const uint64_t* tbl;  // obstacle-window table of the team radius, shared memory
+    const uint64_t* rows; // obstacle rows of the env (used without a table)
+    uint64_t* ob;         // obs words of the env's first emitting agent, global
+    uint8_t* unp;         // unpacked bytes of the slot (null unless exported)
+    const SlotRec* slot;  // slot records of the env's agents
+    uint32_t sh, xmask, side, rw;
+    int ai0;              // emitting index of agent 0 of the team base
+    bool emits, use_table;
+};
+
+template <int A, bool TA>
+__device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, const uint32_t (&X4)[(A + 3) / 4],
+                                               const uint32_t (&Y4)[(A + 3) / 4], const uint32_t (&P4)[(A + 3) / 4],
+                                               uint32_t (&seenf)[(A + 3) / 4]) {
+    constexpr int NS = (A + 1) / 2, NW = (A + 3) / 4;
+    const uint32_t D = 2u * R + 1u;
+    const uint32_t KR = (0x80u + R) * 0x01010101u;
+    const uint32_t C2 = (0x7fu - 2u * R) * 0x01010101u;
+    const uint32_t KP = R * D + R;
+    const uint32_t centre = ~shl_clamp(1u, KP), centre_hi = ~shl_clamp(1u, KP - 32u);
+#pragma unroll 1
+    for (int a = TA ? NS : 0; a < (TA ? A : NS); ++a) {
+        const uint32_t v = T.src[a] & 0x0fffu;
+        const uint32_t xa = v & T.xmask, ya = v >> T.sh;
+        const uint32_t Kx = KR - xa * 0x01010101u, Ky = KR - ya * 0x01010101u;
+        const uint32_t Kp = ((KP - (ya * D + xa)) & 0xffu) * 0x01010101u;
+        const uint32_t Kp7 = Kp & 0x7f7f7f7fu;
+        uint32_t al0 = 0, al1 = 0, op0 = 0, op1 = 0;
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            const uint32_t vx = X4[j] + Kx, vy = Y4[j] + Ky;
+            const uint32_t wx = (vx & 0x7f7f7f7fu) + C2, wy = (vy & 0x7f7f7f7fu) + C2;
+            const uint32_t fail = (~vx | wx | ~vy | wy) & 0x80808080u;
+            if (!TA) {
+                uint32_t hid = 0;  // bytes of hiders in this word
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (4 * j + q >= NS && 4 * j + q < A) hid |= 0x80u << (8 * q);
+                seenf[j] |= ~fail & hid;
+            }
+            const uint32_t n4 = (((P4[j] & 0x7f7f7f7fu) + Kp7) ^ ((P4[j] ^ Kp) & 0x80808080u)) | fail;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int b = 4 * j + q;
+                if (b >= A) continue;
+                const uint32_t n = __byte_perm(n4, 0u, 0x4440u | (uint32_t)q);
+                const uint32_t m0 = shl_clamp(1u, n), m1 = shl_clamp(1u, n - 32u);
+                if ((b >= NS) == TA) {
+                    al0 |= m0;
+                    al1 |= m1;
+                } else {
+                    op0 |= m0;
+                    op1 |= m1;
+                }
+            }
+        }
+        if (!T.emits) continue;
+        al0 &= centre;
+        al1 &= centre_hi;
+        // a5 obstacle plane and the agent's three words
+        uint64_t o0;
+        if (T.use_table) {
+            o0 = T.tbl[ya * T.side + xa];
+        } else {
+            uint64_t unused;
+            obstacle_plane(T.rows, (int)T.rw, (int)xa, (int)ya, (int)R, o0, unused);
+        }
+        const uint64_t al = (uint64_t)al0 | ((uint64_t)al1 << 32);
+        const uint64_t op = (uint64_t)op0 | ((uint64_t)op1 << 32);
+        uint64_t* o = T.ob + 3 * (a - T.ai0);
+        o[0] = o0;
+        o[1] = al;
+        o[2] = op;
+        if (T.unp) {
+            uint8_t* u = T.unp + T.slot[a].unp_rel;
+            const uint32_t DD = D * D;
+            for (uint32_t q = 0; q < DD; ++q) {
+                u[q] = (uint8_t)((o0 >> q) & 1u);
+                u[DD + q] = (uint8_t)((al >> q) & 1u);
+                u[2 * DD + q] = (uint8_t)((op >> q) & 1u);
+            }
+        }
+    }
+}
+
+template <int A>
+__device__ __forceinline__ void emit_segment_fast(const StepParams& P, const CtaShared& H, const EmitCtx& C,
+                                                  uint32_t k, uint32_t e) {
+    constexpr int NS = (A + 1) / 2, NW = (A + 3) / 4;
+    const GroupPlan& L = H.plan;
+    const EnvRT E = H.env[e];  // a register copy: the stores below cannot alias it
+    const uint32_t nsl = L.n_slots;
+    const uint32_t sh = cell_shift(E), xmask = (1u << sh) - 1u;
+    const int first = L.first_slot[e];
+    const uint16_t* Tk = C.T + k * nsl + first;
+    const bool done = (Tk[0] & kDoneBit) != 0u;
+    const uint16_t* src = done ? (H.p0 + first) : Tk;  // observed positions
+    const uint32_t rs = E.r_seek, rh = E.r_hide, Ds = 2u * rs + 1u, Dh = 2u * rh + 1u;
+    uint32_t X4[NW], Y4[NW], Ps[NW], Ph[NW], seenf[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) X4[j] = Y4[j] = Ps[j] = Ph[j] = seenf[j] = 0u;
+#pragma unroll
+    for (int b = 0; b < A; ++b) {
+        const uint32_t v = src[b] & 0x0fffu;
+        const uint32_t x = v & xmask, y = v >> sh;
+        const int j = b >> 2, s8 = 8 * (b & 3);
+        X4[j] |= x << s8;
+        Y4[j] |= y << s8;
+        Ps[j] |= ((y * Ds + x) & 0xffu) << s8;
+        Ph[j] |= ((y * Dh + x) & 0xffu) << s8;
+    }
+    uint32_t sl = C.base_slot + k;
+    if (sl >= P.ring) sl -= P.ring;
+    const bool emit_s = team_emits(E, 0), emit_h = team_emits(E, 1);
+    TeamCtx T;
+    T.src = src;
+    T.rows = C.rows + L.rows_off[e];
+    T.ob = P.obs + (uint64_t)sl * P.obs_words + E.obs_off;
+    T.unp = P.unp ? P.unp + (uint64_t)sl * P.unp_bytes : nullptr;
+    T.slot = H.slot + first;
+    T.sh = sh;
+    T.xmask = xmask;
+    T.side = E.side;
+    T.rw = E.rw;
+    T.use_table = L.flags & kUseTable;
+    T.tbl = C.tbl + L.tbl_off[e][0];
+    T.ai0 = 0;
+    T.emits = emit_s;
+    emit_team_fast<A, false>(T, rs, X4, Y4, Ps, seenf);
+    if (A > 1 && emit_h) {
+        T.tbl = C.tbl + L.tbl_off[e][1];
+        T.ai0 = emit_s ? 0 : NS;
+        T.emits = true;
+        emit_team_fast<A, true>(T, rh, X4, Y4, Ph, seenf);
+    }
+    uint32_t seen = 0;
+    if (done) {
+        seen = seen_pre_reset(Tk, A, NS, (int)rs, sh);
+    } else {
+#pragma unroll
+        for (int b = NS; b < A; ++b) seen |= ((seenf[b >> 2] >> (8 * (b & 3) + 7)) & 1u) << b;
+    }
+    // a6 rewards, a7 done byte, actions
+    const int32_t n_seen = (int32_t)__popc(seen);
+    int32_t* rw = P.rew + (uint64_t)sl * P.agents + E.agent_off;
+    uint8_t* dn = P.done + (uint64_t)sl * P.n_envs + H.gidx[e];
+#pragma unroll
+    for (int a = 0; a < A; ++a) rw[a] = a < NS ? n_seen : -(int32_t)((seen >> a) & 1u);
+    *dn = done ? 3u : 0u;
+    if (P.act_out) {
+        uint8_t* ao = P.act_out + (uint64_t)sl * P.agents + E.agent_off;
+#pragma unroll
+        for (int a = 0; a < A; ++a) ao[a] = C.act[act_index(k, (uint32_t)(first + a), nsl)];
+    }
+}
+
+template <int A>
+__device__ __forceinline__ void emit_segments_fast(const StepParams& P, const CtaShared& H, const EmitCtx& C) {
+    const uint32_t ne = H.plan.n_envs;
+    const uint32_t total = C.len * ne;
+    const uint32_t dk = (uint32_t)C.n_workers / ne, de = (uint32_t)C.n_workers % ne;
+    uint32_t k = (uint32_t)C.worker / ne, e = (uint32_t)C.worker % ne;
+    for (uint32_t it = (uint32_t)C.worker; it < total; it += (uint32_t)C.n_workers) {
+        emit_segment_fast<A>(P, H, C, k, e);
+        e += de;
+        k += dk;
+        if (e >= ne) {
+            e -= ne;
+            ++k;
+        }
+    }
+}
+
+__device__ __forceinline__ void emit_fast_dispatch(int A, const StepParams& P, const CtaShared& H,
+                                                   const EmitCtx& C) {
+    switch (A) {
+        case 1: emit_segments_fast<1>(P, H, C); break;
+        case 2: emit_segments_fast<2>(P, H, C); break;
+        case 3: emit_segments_fast<3>(P, H, C); break;
+        case 4: emit_segments_fast<4>(P, H, C); break;
+        case 5: emit_segments_fast<5>(P, H, C); break;
+        case 6: emit_segments_fast<6>(P, H, C); break;
+        case 7: emit_segments_fast<7>(P, H, C); break;
+        case 8: emit_segments_fast<8>(P, H, C); break;
+        case 9: emit_segments_fast<9>(P, H, C); break;
+        case 10: emit_segments_fast<10>(P, H, C); break;
+        case 11: emit_segments_fast<11>(P, H, C); break;
+        case 12: emit_segments_fast<12>(P, H, C); break;
+        case 13: emit_segments_fast<13>(P, H, C); break;
+        case 14: emit_segments_fast<14>(P, H, C); break;
+        case 15: emit_segments_fast<15>(P, H, C); break;
+        default: emit_segments_fast<16>(P, H, C); break;
+    }
+}
+
 // Per-cell shared state of the dynamics: a claim word (byte a-1 holds the
 // lane claiming the cell through action a, 1 N 2 S 3 E 4 W; 0xff = none)
 // and a state byte (bits 1..4: action a leads onto a free cell of the grid;
@@ -523,6 +764,8 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
         const SlotRec& r = H.slot[sidx];
         const EnvRT& E = H.env[r.env];
         H.slot[sidx].p0 = (uint16_t)to_cta(P.start[E.agent_off + r.agent], cell_shift(E));
+        H.p0[sidx] = H.slot[sidx].p0;
+        H.key[sidx] = make_uint2(r.agent, E.env_id);
     }
     __syncthreads();
     // cell state and claims, obstacle-window tables (plane 0 of every cell
@@ -573,34 +816,47 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
 
     const uint32_t n_chunks = (P.n_steps + kc - 1) / kc;
 
-    // a1: Philox actions of chunk c into buffer c % 3.  Worker w serves slot
-    // w % nsl and every (n_workers / nsl)-th Philox block; one block serves
-    // four consecutive steps.
+    // a1: Philox actions of chunk c into buffer c % 3.  One Philox block
+    // (counter word 0 = step >> 2) serves four consecutive steps of one
+    // agent slot; work items are (block, slot) pairs, slot fastest, and a
+    // thread draws two items at a time (independent rounds interleave).
+    // When the chunk starts on a block boundary a block fills one u32 word
+    // of the buffer (byte k & 3 of word (k >> 2) nsl + s is step k of slot s).
     auto draw_actions = [&](uint32_t c, int worker, int n_workers) {
         const uint64_t ts = P.t0 + (uint64_t)c * kc;
         const uint32_t len = min(kc, P.n_steps - c * kc);
-        const uint64_t te = ts + len;
         const uint64_t b0 = ts >> 2;
-        const uint32_t nblk = (uint32_t)(((te - 1) >> 2) - b0 + 1);
-        uint8_t* A = s_act + (c % 3u) * act_bytes;
-        const int per = max(1, n_workers / nsl);
-        const int s_first = worker % nsl, sub = worker / nsl;
-        if (n_workers >= nsl && sub >= per) return;
-        for (int s = s_first; s < nsl; s += (n_workers >= nsl ? nsl : n_workers)) {
-            const SlotRec& r = H.slot[s];
-            const uint32_t agent = r.agent;
-            const uint32_t env_id = H.env[r.env].env_id;
-            for (uint32_t bi = (n_workers >= nsl ? sub : 0); bi < nblk; bi += per) {
-                uint32_t c0 = (uint32_t)(b0 + bi), c1 = agent, c2 = env_id, c3 = 0u;
-                philox4x32_10(c0, c1, c2, c3, P.key0, P.key1);
-                const uint32_t u[4] = {c0, c1, c2, c3};
+        const uint32_t off = (uint32_t)(ts & 3u);
+        const uint32_t nblk = (off + len + 3u) >> 2;
+        uint8_t* A8 = s_act + (c % 3u) * act_bytes;
+        uint32_t* A32 = reinterpret_cast<uint32_t*>(A8);
+        const uint32_t ns = (uint32_t)nsl;
+        const uint32_t n_items = nblk * ns;
+        const uint32_t stride = 2u * (uint32_t)n_workers;
+        auto put = [&](uint32_t it, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+            const uint32_t s = it % ns, bi = it / ns;
+            const uint32_t w = mulhi_n(c0, 5u) | (mulhi_n(c1, 5u) << 8) | (mulhi_n(c2, 5u) << 16) |
+                               (mulhi_n(c3, 5u) << 24);
+            if (off == 0u) {
+                A32[bi * ns + s] = w;
+            } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint64_t t = (b0 + bi) * 4 + j;
-                    if (t >= ts && t < te) A[act_index((uint32_t)(t - ts), s, nsl)] = (uint8_t)mulhi_n(u[j], 5u);
+                for (uint32_t j = 0; j < 4; ++j) {
+                    const uint32_t k = 4u * bi + j - off;  // wraps past len below 0
+                    if (k < len) A8[act_index(k, s, ns)] = (uint8_t)(w >> (8u * j));
                 }
             }
-            if (n_workers >= nsl) break;
+        };
+        for (uint32_t it = (uint32_t)worker; it < n_items; it += stride) {
+            const uint32_t it2 = it + (uint32_t)n_workers;
+            const bool two = it2 < n_items;
+            const uint2 ka = H.key[it % ns], kb = H.key[(two ? it2 : it) % ns];
+            uint32_t a0 = (uint32_t)(b0 + it / ns), a1 = ka.x, a2 = ka.y, a3 = 0u;
+            uint32_t d0 = (uint32_t)(b0 + (two ? it2 : it) / ns), d1 = kb.x, d2 = kb.y, d3 = 0u;
+            philox4x32_10(a0, a1, a2, a3, P.key0, P.key1);
+            philox4x32_10(d0, d1, d2, d3, P.key0, P.key1);
+            put(it, a0, a1, a2, a3);
+            if (two) put(it2, d0, d1, d2, d3);
         }
     };
 
@@ -723,6 +979,9 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
     const int worker = tid - n_dyn * 32;
     const int n_workers = M * 32;
     const bool wide = H.env[0].wpp == 2;  // the group shares its radii
+    // one thread per (step, env) when the seekers are ceil(A/2) and every
+    // window fits one word; else one lane per agent
+    const bool fast = fast_emission(H.env[0]);
     for (uint32_t c = 0; c <= n_chunks; ++c) {
         if (c >= 1) {
             const uint32_t cp = c - 1;
@@ -735,7 +994,9 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             C.base_slot = (uint32_t)(((uint64_t)P.slot0 + (uint64_t)cp * kc) % P.ring);
             C.worker = worker;
             C.n_workers = n_workers;
-            if (wide)
+            if (fast)
+                emit_fast_dispatch(H.env[0].n_agents, P, H, C);
+            else if (wide)
                 emit_chunk<3>(P, H, C, warp - n_dyn, M, lane);
             else
                 emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
@@ -778,16 +1039,12 @@ static cudaError_t launch_step_t(const StepParams& p, uint32_t n_groups, uint32_
     return cudaGetLastError();
 }
 
-// The register budget follows the CTA size: up to 128 registers a thread
-// (the emission thread keeps a whole env's positions in registers), so CTAs
-// of 64 / 96 / 128 threads keep 8 / 5 / 4 resident per SM when the groups
-// run in waves; the persistent one-CTA-per-SM shapes use up to 512 threads.
+// One instantiation: every CTA shape (64..512 threads) runs with a cap of
+// 128 registers a thread, which is what 512 threads x 1 CTA leaves and also
+// what 64 threads x 8 CTAs would; residency is then set by shared memory.
 cudaError_t launch_step(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
                         cudaStream_t st) {
     if (n_groups == 0 || p.n_steps == 0) return cudaSuccess;
-    if (threads <= 64) return launch_step_t<64, 8>(p, n_groups, threads, smem, st);
-    if (threads <= 96) return launch_step_t<96, 5>(p, n_groups, threads, smem, st);
-    if (threads <= 128) return launch_step_t<128, 4>(p, n_groups, threads, smem, st);
     if (threads <= 512) return launch_step_t<512, 1>(p, n_groups, threads, smem, st);
     return cudaErrorInvalidConfiguration;
 }
