@@ -58,6 +58,29 @@ def algorithmic_bytes_per_env_step(descs, n_envs, unpacked):
     return total / n_envs
 
 
+def measured_traffic(workload_name):
+    """DRAM bytes per env-step of step_kernel from the committed ncu summary
+    of this workload, or None when the summary is missing or was taken on
+    other kernel sources (the summary records their digest)."""
+    from paper_2604_27162_gb300 import build as B
+
+    path = os.path.join(ROOT, "profiles", "step_kernel_%s.md" % workload_name)
+    try:
+        with open(path) as f:
+            text = f.read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        if "=" in line and line.split("=", 1)[0] in ("traffic_bytes_per_env_step", "source_digest"):
+            key, val = line.split("=", 1)
+            vals[key] = val.strip()
+    if vals.get("source_digest") != B.source_digest() or "traffic_bytes_per_env_step" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_env_step"])
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -129,6 +152,7 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_2604_27162_gb300 import hase
+    from paper_2604_27162_gb300 import shard as S
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -144,7 +168,7 @@ def run_gpu(args):
     # weak scaling: rank r steps envs [r*E, (r+1)*E) of the global batch
     stream = torch.cuda.current_stream()
     eng = hase.Engine(n_envs, c["seed"], c["descs"], ring_steps=run, flags=flags,
-                      env_id_base=rank * n_envs, stream=stream)
+                      env_id_base=S.env_base(rank, n_envs), stream=stream)
     info = eng.launch_info()
     spl = info["steps_per_launch"] or 65536
     launches_per_step = math.ceil(run / spl)
@@ -173,17 +197,15 @@ def run_gpu(args):
         dist.barrier()
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    env_steps = n_envs * run * args.steps * world
+    ms = S.max_over_ranks(ms, device="cuda")
     agents = sum(c["descs"][0 if len(c["descs"]) == 1 else e]["n_agents"] for e in range(n_envs))
-    value = env_steps / (ms / 1e3)
+    value = S.weak_throughput(n_envs * run * args.steps, world, ms / 1e3)
     bpe = algorithmic_bytes_per_env_step(c["descs"], n_envs, c["unpacked"])
     per_rank_bytes = bpe * n_envs * run * args.steps
     achieved = per_rank_bytes / (ms / 1e3) / 1e9
     peak, peak_kind = peaks()
+    tpe = measured_traffic(args.workload)
+    traffic = tpe * n_envs * run if tpe is not None else None  # bytes per launch
 
     # end to end through the public API: every step's results copied to
     # pinned host memory inside the timed region (no per-step inputs exist:
@@ -222,11 +244,12 @@ def run_gpu(args):
                 "kernel": "step_kernel",
                 "achieved": achieved,
                 "peak": peak,
-                "peak_kind": peak_kind,
+                "peak_kind": peak_kind + " (HBM copy burst, kernel timed alone)",
                 "unit": "GB/s",
                 "frac": achieved / peak,
                 "algorithmic_bytes_per_env_step": bpe,
-                "traffic": None,
+                "algorithmic_bytes_per_launch": bpe * n_envs * run,
+                "traffic": traffic,
             },
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clk,
@@ -242,8 +265,9 @@ def run_e2e(eng, c, run, stream, args):
     import torch
 
     n_steps = run * max(1, min(args.steps, 3))
-    chunk = min(1000, run)
     L = eng.layout
+    per_step = L["obs_words"] * 8 + L["agents"] * 4 + eng.n_envs + (L["unp_bytes"] if eng.unpacked is not None else 0)
+    chunk = max(1, min(1000, run, (1 << 30) // per_step))  # pinned staging of at most 1 GiB
     h_obs = torch.empty((chunk, L["obs_words"]), dtype=torch.int64, pin_memory=True)
     h_rew = torch.empty((chunk, L["agents"]), dtype=torch.int32, pin_memory=True)
     h_done = torch.empty((chunk, eng.n_envs), dtype=torch.uint8, pin_memory=True)
@@ -283,9 +307,31 @@ def run_e2e(eng, c, run, stream, args):
             "note": "per env-step: every env's obs, reward and done copied to pinned host memory"}
 
 
-def cpu_baseline(c, args, target_s=12.0):
+def _oracle_shard(job):
+    """One host process of the multi-core oracle leg: its env range of the
+    workload stepped for about `seconds`."""
+    n, base, seed, descs, unpacked, seconds = job
+    sys.path.insert(0, ROOT)
+    import oracle
+
+    w = oracle.World(n, seed, descs, env_id_base=base)
+    t = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t < seconds:
+        w.step(unpacked=unpacked)
+        steps += 1
+    dt = time.perf_counter() - t
+    w.close()
+    return n, steps, dt
+
+
+def cpu_baseline(c, args, target_s=8.0):
     """The oracle (single-threaded C, as it stands) on a bounded sample of the
-    same workload: all envs of the batch for as many steps as fit ~target_s."""
+    same workload: all envs of the batch for as many steps as fit target_s,
+    on one core and as one process per host core over env shards (spawned:
+    the parent holds a CUDA context)."""
+    import multiprocessing as mp
+
     import oracle
 
     n = c["n_envs"]
@@ -296,8 +342,25 @@ def cpu_baseline(c, args, target_s=12.0):
         w.step(unpacked=c["unpacked"])
         steps += 1
     dt = time.perf_counter() - t
-    return {"value": n * steps / dt, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d envs x %d steps of the workload (%.1f s)" % (n, steps, dt)}
+    single = {"value": n * steps / dt, "unit": "env-steps/s", "cores": 1,
+              "sample": "%d envs x %d steps (%.1f s)" % (n, steps, dt)}
+    cores = max(1, min(os.cpu_count() or 1, n))
+    jobs = []
+    for i in range(cores):
+        lo, hi = i * n // cores, (i + 1) * n // cores
+        d = c["descs"] if len(c["descs"]) == 1 else c["descs"][lo:hi]
+        jobs.append((hi - lo, lo, c["seed"], d, c["unpacked"], target_s))
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_shard, jobs)
+        value = sum(r[0] * r[1] / r[2] for r in res)
+        return {"value": value, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+                "sample": "%d envs in %d shards, %d-%d steps each (~%.0f s), one process per core"
+                          % (n, cores, min(r[1] for r in res), max(r[1] for r in res), target_s),
+                "single_core": single}
+    except Exception as exc:  # no pool possible: report the single-core leg
+        single.update({"kind": "oracle", "note": "multi-core leg failed: %s" % exc})
+        return single
 
 
 def run_reference(args):
@@ -355,7 +418,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ten1k", choices=sorted(RUN_STEPS))
