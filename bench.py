@@ -147,6 +147,79 @@ def workload(name):
     return c
 
 
+def shape_classes(descs, n_envs):
+    """Env indices grouped by kernel shape (everything but the obstacle
+    density): the 'per-config' form launches one engine per class."""
+    classes = {}
+    for e in range(n_envs):
+        d = descs[0 if len(descs) == 1 else e]
+        key = (d["side"], d["n_agents"], d["n_seekers"], d["r_seek"], d["r_hide"], d["cap"], d["obs_teams"])
+        classes.setdefault(key, []).append(e)
+    return classes
+
+
+def build_form(form, c, run, flags, stream, base, log):
+    """Engines and the benchmark step of one form of the workload.
+    plain:      one engine, default launch configuration, hase_step;
+    batched:    one engine, autotuned configuration, the rollout replayed as
+                a CUDA graph (hase_step_graph);
+    per-config: one engine per kernel-shape class of the batch, launched one
+                after another on the stream (each class's envs get their
+                own env-id range, so its trajectories differ from the
+                batched run's while the workload is the same)."""
+    from paper_2604_27162_gb300 import autotune, hase
+
+    n_envs = c["n_envs"]
+    extra = {"form": form}
+    if form == "per-config":
+        engines = []
+        next_id = base
+        for key, idx in sorted(shape_classes(c["descs"], n_envs).items()):
+            descs = [c["descs"][0 if len(c["descs"]) == 1 else e] for e in idx]
+            engines.append(hase.Engine(len(idx), c["seed"], descs, ring_steps=run, flags=flags,
+                                       env_id_base=next_id, stream=stream))
+            next_id += len(idx)
+        extra["classes"] = len(engines)
+
+        def step():
+            for eng in engines:
+                eng.step(run)
+        launches = sum(math.ceil(run / (e.launch_info()["steps_per_launch"] or 65536)) + 1 for e in engines)
+        return engines, step, launches, extra
+    setting = {}
+    if form == "batched":
+        t = time.perf_counter()
+        setting, trials = autotune.tune(n_envs, c["seed"], c["descs"], flags, stream=stream, log=log)
+        extra["autotune"] = {"setting": setting, "trials": len(trials),
+                             "seconds": round(time.perf_counter() - t, 1)}
+    eng = hase.Engine(n_envs, c["seed"], c["descs"], ring_steps=run, flags=flags, env_id_base=base,
+                      stream=stream, **setting)
+    spl = eng.launch_info()["steps_per_launch"] or 65536
+    if form == "batched":
+        def step():
+            eng.step_graph(run)
+    else:
+        def step():
+            eng.step(run)
+    return [eng], step, math.ceil(run / spl) + 1, extra
+
+
+def time_form(step, steps, warmup, stream):
+    import torch
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -167,14 +240,12 @@ def run_gpu(args):
     flags = hase.HASE_EXPORT_UNPACKED if c["unpacked"] else 0
     # weak scaling: rank r steps envs [r*E, (r+1)*E) of the global batch
     stream = torch.cuda.current_stream()
-    eng = hase.Engine(n_envs, c["seed"], c["descs"], ring_steps=run, flags=flags,
-                      env_id_base=S.env_base(rank, n_envs), stream=stream)
+    form = args.form or ("batched" if args.workload == "uneven64k" else "plain")
+    log = (lambda m: print(m, file=sys.stderr)) if rank == 0 else None
+    engines, one_step, launches_per_step, form_info = build_form(
+        form, c, run, flags, stream, S.env_base(rank, n_envs), log)
+    eng = engines[0]
     info = eng.launch_info()
-    spl = info["steps_per_launch"] or 65536
-    launches_per_step = math.ceil(run / spl)
-
-    def one_step():
-        eng.step(run)
 
     for _ in range(args.warmup):
         one_step()
@@ -210,8 +281,18 @@ def run_gpu(args):
     # end to end through the public API: every step's results copied to
     # pinned host memory inside the timed region (no per-step inputs exist:
     # actions are drawn on the device)
-    e2e = None if args.no_e2e else run_e2e(eng, c, run, stream, args)
-    eng.close()
+    e2e = None if args.no_e2e or len(engines) > 1 else run_e2e(eng, c, run, stream, args)
+    # the batched form is reported against the other two forms on this GPU
+    if form == "batched" and rank == 0 and not args.no_compare:
+        cmp_steps = max(3, min(args.steps, 20))
+        for other in ("plain", "per-config"):
+            en2, st2, _, _ = build_form(other, c, run, flags, stream, 0, None)
+            ms2 = time_form(st2, cmp_steps, 2, stream)
+            form_info["%s_env_steps_per_s" % other.replace("-", "_")] = n_envs * run * cmp_steps / (ms2 / 1e3)
+            for e2 in en2:
+                e2.close()
+    for e in engines:
+        e.close()
     if rank == 0:
         out = {
             "metric": "env-steps/s",
@@ -238,6 +319,7 @@ def run_gpu(args):
                 "threads_per_cta": info["threads"],
                 "smem_per_cta": info["smem"],
                 "parallelism": "env shards, one process per GPU" if world > 1 else "1 GPU",
+                **form_info,
             },
             "roofline": {
                 "bound": "hbm",
@@ -426,6 +508,10 @@ def main():
     ap.add_argument("--run-steps", type=int, default=0,
                     help="override the env-steps per benchmark step (small profiling cases)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--form", choices=["plain", "batched", "per-config"], default=None,
+                    help="launch form (default: batched for uneven64k, plain otherwise)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="batched form: skip timing the plain and per-config forms beside it")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

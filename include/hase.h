@@ -109,6 +109,10 @@ typedef struct hase_config {
     uint32_t chunk_steps;        /* steps per on-chip chunk (1..32), 0 = auto  */
     uint32_t emit_warps;         /* output warps per CTA (1..12), 0 = auto     */
     uint32_t max_group_envs;     /* envs packed per CTA (1..64), 0 = auto      */
+    uint32_t smem_cap;           /* dynamic shared memory per CTA in bytes     */
+                                 /* (16384..221184), 0 = 221184: smaller caps  */
+                                 /* pack fewer envs per CTA and drop window    */
+                                 /* tables, so that more CTAs fit on an SM     */
 } hase_config;
 
 /* Sizes and per-env offsets of one ring slot.  The offset arrays are host
@@ -147,6 +151,15 @@ hase_status hase_reward_ptr(hase_handle *h, int32_t **reward);
 hase_status hase_done_ptr(hase_handle *h, uint8_t **done);
 hase_status hase_actions_ptr(hase_handle *h, uint8_t **actions);
 hase_status hase_layout_get(hase_handle *h, hase_layout *out);
+
+/* The same n_steps as one CUDA graph: the first call for a given n_steps
+ * captures the launches hase_step would enqueue (on an internal stream) and
+ * instantiates them; every call then launches the graph on `stream`.  The
+ * kernels read the step counter from device memory, so one graph serves
+ * every replay.  The capture allocates host-side graph objects only, and
+ * must not itself run inside another stream capture.  Graphs are freed by
+ * hase_destroy.  Not in the paper: a launch-overhead device of this engine. */
+hase_status hase_step_graph(hase_handle *h, uint32_t n_steps, void *stream);
 
 /* Steps taken since create / reset. */
 hase_status hase_step_count(hase_handle *h, uint64_t *t);

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -20,6 +21,8 @@ cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* po
                            const uint64_t* rows, uint64_t* obs, uint8_t* unp, cudaStream_t st);
 cudaError_t launch_step(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
                         cudaStream_t st);
+cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st);
+cudaError_t prepare_step(uint32_t smem);
 }  // namespace hase
 
 using namespace hase;
@@ -35,7 +38,11 @@ struct hase_handle {
     std::vector<uint64_t> agent_off, obs_off, unp_off;
     uint64_t agents = 0, obs_words = 0, unp_bytes = 0, rows_words = 0;
     uint32_t smem = 0, threads = 0, kc = 16, emit_warps = 0, steps_per_launch = 0, n_dyn = 1;
+    uint32_t smem_budget = kSmemBudget;
     uint64_t t = 0;
+    uint64_t* d_clock = nullptr;  // steps enqueued before the running launch
+    cudaStream_t cap_stream = nullptr;
+    std::map<uint32_t, cudaGraphExec_t> graphs;
     // device memory
     EnvRT* d_env = nullptr;
     EnvState* d_est = nullptr;
@@ -82,9 +89,14 @@ static hase_status cuda_fail(hase_handle* h, cudaError_t e, const char* what) {
 
 static void free_all(hase_handle* h) {
     void* ptrs[] = {h->d_env, h->d_est,  h->d_pos, h->d_start, h->d_rows, h->d_groups,
-                    h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr, h->d_env_list};
+                    h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr, h->d_env_list,
+                    h->d_clock};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+    h->graphs.clear();
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->cap_stream = nullptr;
 }
 
 static bool emits(const hase_env_desc& d, uint32_t a) {
@@ -124,7 +136,7 @@ static uint64_t shape_key(const EnvRT& E) {
            (uint64_t)E.n_seekers;
 }
 
-static void make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
+static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
     const uint32_t E = h->n_envs;
     h->env_list.resize(E);
     for (uint32_t e = 0; e < E; ++e) h->env_list[e] = e;
@@ -162,7 +174,7 @@ static void make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             genv.push_back(En);
             uint16_t flags = 0;
             if (!plan_group(genv.data(), (int)genv.size(), (int)h->kc, flags, plan) ||
-                plan.total > kSmemBudget) {
+                plan.total > h->smem_budget) {
                 genv.pop_back();
                 break;
             }
@@ -170,9 +182,10 @@ static void make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             g.n_envs += 1;
             ++i;
         }
+        if (g.n_envs == 0) return false;  // one env alone exceeds the budget
         uint16_t flags = 0;
         plan_group(genv.data(), g.n_envs, (int)h->kc, kUseTable, plan);
-        if (plan.total <= kSmemBudget) flags |= kUseTable;
+        if (plan.total <= h->smem_budget) flags |= kUseTable;
         plan_group(genv.data(), g.n_envs, (int)h->kc, flags, plan);
         g.flags = flags;
         g.n_dyn = (uint8_t)plan.n_dyn;
@@ -182,6 +195,7 @@ static void make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
     }
     h->smem = smem_max;
     h->n_dyn = dyn_max;
+    return true;
 }
 
 extern "C" {
@@ -206,6 +220,8 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if (cfg->emit_warps > 12) return fail(nullptr, HASE_EINVAL, "emit_warps outside 1..12");
     if (cfg->max_group_envs > (uint32_t)kMaxGroupEnvs)
         return fail(nullptr, HASE_EINVAL, "max_group_envs outside 1..%d", kMaxGroupEnvs);
+    if (cfg->smem_cap != 0 && (cfg->smem_cap < 16384u || cfg->smem_cap > kSmemBudget))
+        return fail(nullptr, HASE_EINVAL, "smem_cap outside 16384..%u", kSmemBudget);
     for (uint32_t i = 0; i < cfg->n_desc; ++i) {
         hase_status s = validate(cfg->envs[i], i);
         if (s != HASE_OK) return s;
@@ -274,7 +290,11 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     int n_sm = 0;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device);
     if (n_sm <= 0) n_sm = 1;
-    make_groups(h, cfg->max_group_envs, (uint32_t)n_sm);
+    if (cfg->smem_cap) h->smem_budget = cfg->smem_cap;
+    if (!make_groups(h, cfg->max_group_envs, (uint32_t)n_sm)) {
+        delete h;
+        return fail(nullptr, HASE_EINVAL, "smem_cap %u is too small for one env of this batch", cfg->smem_cap);
+    }
     // emission warps.  Persistent regime (one CTA per SM): four when every
     // group emits one (step, env) per thread (more warps only add store
     // traffic in flight), else twelve; CTAs in waves: six.
@@ -310,6 +330,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if (h->flags & HASE_EXPORT_UNPACKED) HASE_ALLOC(h->d_unp, R * h->unp_bytes);
     HASE_ALLOC(h->d_err, 4);
     HASE_ALLOC(h->d_thr, 4 * h->n_envs);
+    HASE_ALLOC(h->d_clock, 8);
 #undef HASE_ALLOC
     if (ce != cudaSuccess) {
         hase_status s = cuda_fail(nullptr, ce, "cudaMalloc");
@@ -336,6 +357,8 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if ((s = finish(cudaMemsetAsync(h->d_est, 0, sizeof(EnvState) * h->n_envs, st), "memset")) != HASE_OK)
         return s;
     if ((s = finish(cudaMemsetAsync(h->d_err, 0, 4, st), "memset")) != HASE_OK) return s;
+    if ((s = finish(cudaMemsetAsync(h->d_clock, 0, 8, st), "memset")) != HASE_OK) return s;
+    if ((s = finish(prepare_step(h->smem), "shared memory opt-in")) != HASE_OK) return s;
     if ((s = finish(cudaMemsetAsync(h->d_obs, 0, 8 * R * h->obs_words, st), "memset")) != HASE_OK) return s;
     if ((s = finish(cudaMemsetAsync(h->d_rew, 0, 4 * R * h->agents, st), "memset")) != HASE_OK) return s;
     if ((s = finish(cudaMemsetAsync(h->d_done, 0, R * h->n_envs, st), "memset")) != HASE_OK) return s;
@@ -376,20 +399,18 @@ hase_status hase_reset(hase_handle* h, void* stream) {
     if (h->d_act) HASE_CUDA(h, cudaMemsetAsync(h->d_act + last * h->agents, 0, h->agents, st));
     HASE_CUDA(h, launch_observe(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_obs + last * h->obs_words,
                                 h->d_unp ? h->d_unp + last * h->unp_bytes : nullptr, st));
+    HASE_CUDA(h, cudaMemsetAsync(h->d_clock, 0, 8, st));
     h->t = 0;
     return HASE_OK;
 }
 
-hase_status hase_step(hase_handle* h, uint32_t n_steps, void* stream) {
-    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
-    if (n_steps == 0) return HASE_OK;
-    if (((h->t + n_steps) >> 2) > 0xffffffffull)
-        return fail(h, HASE_EINVAL, "step counter would exceed 2^34 (Philox counter word)");
-    cudaStream_t st = (cudaStream_t)stream;
+// Enqueue the launches of n_steps steps and the counter advance; the kernels
+// read the step count from d_clock, so the same launches replay correctly.
+static hase_status enqueue_steps(hase_handle* h, uint32_t n_steps, cudaStream_t st) {
     const uint32_t K = h->steps_per_launch ? h->steps_per_launch : 65536u;
-    uint32_t left = n_steps;
-    while (left > 0) {
-        const uint32_t n = std::min(left, K);
+    uint32_t done = 0;
+    while (done < n_steps) {
+        const uint32_t n = std::min(n_steps - done, K);
         StepParams p;
         p.env = h->d_env;
         p.est = h->d_est;
@@ -406,10 +427,10 @@ hase_status hase_step(hase_handle* h, uint32_t n_steps, void* stream) {
         p.obs_words = h->obs_words;
         p.agents = h->agents;
         p.unp_bytes = h->unp_bytes;
-        p.t0 = h->t;
+        p.clock = h->d_clock;
+        p.t0 = done;
         p.n_envs = h->n_envs;
         p.ring = h->ring;
-        p.slot0 = (uint32_t)(h->t % h->ring);
         p.n_steps = n;
         p.kc = h->kc;
         p.emit_warps = h->emit_warps;
@@ -417,9 +438,54 @@ hase_status hase_step(hase_handle* h, uint32_t n_steps, void* stream) {
         p.key0 = (uint32_t)(h->seed & 0xffffffffu);
         p.key1 = (uint32_t)(h->seed >> 32);
         HASE_CUDA(h, launch_step(p, (uint32_t)h->groups.size(), h->threads, h->smem, st));
-        h->t += n;
-        left -= n;
+        done += n;
     }
+    HASE_CUDA(h, launch_advance(h->d_clock, n_steps, st));
+    return HASE_OK;
+}
+
+static hase_status check_steps(hase_handle* h, uint32_t n_steps) {
+    if (((h->t + n_steps) >> 2) > 0xffffffffull)
+        return fail(h, HASE_EINVAL, "step counter would exceed 2^34 (Philox counter word)");
+    return HASE_OK;
+}
+
+hase_status hase_step(hase_handle* h, uint32_t n_steps, void* stream) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (n_steps == 0) return HASE_OK;
+    hase_status s = check_steps(h, n_steps);
+    if (s != HASE_OK) return s;
+    s = enqueue_steps(h, n_steps, (cudaStream_t)stream);
+    if (s != HASE_OK) return s;
+    h->t += n_steps;
+    return HASE_OK;
+}
+
+hase_status hase_step_graph(hase_handle* h, uint32_t n_steps, void* stream) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (n_steps == 0) return HASE_OK;
+    hase_status s = check_steps(h, n_steps);
+    if (s != HASE_OK) return s;
+    auto it = h->graphs.find(n_steps);
+    if (it == h->graphs.end()) {
+        if (!h->cap_stream) HASE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        HASE_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        s = enqueue_steps(h, n_steps, h->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (s != HASE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        HASE_CUDA(h, ce);
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        HASE_CUDA(h, ie);
+        it = h->graphs.emplace(n_steps, exec).first;
+    }
+    HASE_CUDA(h, cudaGraphLaunch(it->second, (cudaStream_t)stream));
+    h->t += n_steps;
     return HASE_OK;
 }
 
@@ -514,8 +580,10 @@ hase_status hase_set_state(hase_handle* h, const void* buf, size_t size, void* s
     HASE_CUDA(h, cudaMemcpyAsync(h->d_pos, p, 2 * h->agents, cudaMemcpyHostToDevice, st));
     HASE_CUDA(h, cudaMemcpyAsync(h->d_est, p + 2 * h->agents, sizeof(EnvState) * h->n_envs,
                                  cudaMemcpyHostToDevice, st));
+    const uint64_t tt = hdr[3];
+    HASE_CUDA(h, cudaMemcpyAsync(h->d_clock, &tt, 8, cudaMemcpyHostToDevice, st));
     HASE_CUDA(h, cudaStreamSynchronize(st));
-    h->t = hdr[3];
+    h->t = tt;
     return HASE_OK;
 }
 

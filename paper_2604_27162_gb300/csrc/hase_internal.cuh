@@ -192,10 +192,10 @@ struct StepParams {
     uint64_t obs_words;
     uint64_t agents;
     uint64_t unp_bytes;
-    uint64_t t0;         // global step index of the first step of the launch
+    const uint64_t* clock;  // device step counter (steps taken before this enqueue)
+    uint64_t t0;         // offset of the launch's first step from *clock
     uint32_t n_envs;
     uint32_t ring;
-    uint32_t slot0;      // t0 mod ring
     uint32_t n_steps;
     uint32_t kc;         // steps per chunk (<= kMaxChunk, <= ring)
     uint32_t n_dyn;      // dynamics warps per CTA (the largest group's)

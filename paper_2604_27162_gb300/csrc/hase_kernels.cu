@@ -815,6 +815,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
     }
 
     const uint32_t n_chunks = (P.n_steps + kc - 1) / kc;
+    const uint64_t T0 = *P.clock + P.t0;  // global step index of the launch's first step
 
     // a1: Philox actions of chunk c into buffer c % 3.  One Philox block
     // (counter word 0 = step >> 2) serves four consecutive steps of one
@@ -823,7 +824,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
     // When the chunk starts on a block boundary a block fills one u32 word
     // of the buffer (byte k & 3 of word (k >> 2) nsl + s is step k of slot s).
     auto draw_actions = [&](uint32_t c, int worker, int n_workers) {
-        const uint64_t ts = P.t0 + (uint64_t)c * kc;
+        const uint64_t ts = T0 + (uint64_t)c * kc;
         const uint32_t len = min(kc, P.n_steps - c * kc);
         const uint64_t b0 = ts >> 2;
         const uint32_t off = (uint32_t)(ts & 3u);
@@ -991,7 +992,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             C.act = s_act + (cp % 3u) * act_bytes;
             C.rows = s_rows;
             C.tbl = s_tbl;
-            C.base_slot = (uint32_t)(((uint64_t)P.slot0 + (uint64_t)cp * kc) % P.ring);
+            C.base_slot = (uint32_t)((T0 + (uint64_t)cp * kc) % P.ring);
             C.worker = worker;
             C.n_workers = n_workers;
             if (fast)
@@ -1027,14 +1028,23 @@ cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* po
     return cudaGetLastError();
 }
 
+// The device step counter moves on once the launches of an enqueue are in.
+__global__ void advance_kernel(uint64_t* clock, uint32_t n) { *clock += n; }
+
+cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st) {
+    advance_kernel<<<1, 1, 0, st>>>(clock, n);
+    return cudaGetLastError();
+}
+
+// Opt in to the shared memory of the largest CTA once, outside any capture.
+cudaError_t prepare_step(uint32_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(step_kernel<512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 template <int MAXT, int MINB>
 static cudaError_t launch_step_t(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
                                  cudaStream_t st) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<MAXT, MINB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     step_kernel<MAXT, MINB><<<n_groups, threads, smem, st>>>(p);
     return cudaGetLastError();
 }

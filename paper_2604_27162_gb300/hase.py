@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA
 
 # Every symbol include/hase.h declares (the CPU tests check the export list).
 EXPORTS = [
-    "hase_create", "hase_reset", "hase_step", "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
+    "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
     "hase_actions_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
     "hase_get_world", "hase_sync", "hase_launch_info", "hase_destroy", "hase_last_error",
 ]
@@ -59,6 +59,7 @@ class hase_config(C.Structure):
         ("chunk_steps", C.c_uint32),
         ("emit_warps", C.c_uint32),
         ("max_group_envs", C.c_uint32),
+        ("smem_cap", C.c_uint32),
     ]
 
 
@@ -92,6 +93,7 @@ def load(path=LIB_PATH):
     L.hase_create.argtypes = [C.POINTER(hase_config), P, C.POINTER(H)]
     L.hase_reset.argtypes = [H, P]
     L.hase_step.argtypes = [H, u32, P]
+    L.hase_step_graph.argtypes = [H, u32, P]
     L.hase_obs_ptr.argtypes = [H, C.POINTER(P), C.POINTER(P)]
     L.hase_reward_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_done_ptr.argtypes = [H, C.POINTER(P)]
@@ -132,7 +134,7 @@ def _stream(stream):
 # C names, one to one.
 # ---------------------------------------------------------------------------
 def make_config(n_envs, seed, descs, ring_steps, flags=0, env_id_base=0, steps_per_launch=0,
-                chunk_steps=0, emit_warps=0, max_group_envs=0):
+                chunk_steps=0, emit_warps=0, max_group_envs=0, smem_cap=0):
     arr = (hase_env_desc * len(descs))()
     for i, d in enumerate(descs):
         for k, _ in hase_env_desc._fields_:
@@ -140,7 +142,8 @@ def make_config(n_envs, seed, descs, ring_steps, flags=0, env_id_base=0, steps_p
     cfg = hase_config(n_envs=n_envs, env_id_base=env_id_base, seed=seed & (2**64 - 1),
                       envs=C.cast(arr, C.POINTER(hase_env_desc)), n_desc=len(descs),
                       ring_steps=ring_steps, flags=flags, steps_per_launch=steps_per_launch,
-                      chunk_steps=chunk_steps, emit_warps=emit_warps, max_group_envs=max_group_envs)
+                      chunk_steps=chunk_steps, emit_warps=emit_warps, max_group_envs=max_group_envs,
+                      smem_cap=smem_cap)
     cfg._keep = arr  # keep the descriptor array alive
     return cfg
 
@@ -157,6 +160,10 @@ def hase_reset(h, stream=None):
 
 def hase_step(h, n_steps, stream=None):
     _check(load().hase_step(h, n_steps, _stream(stream)), h)
+
+
+def hase_step_graph(h, n_steps, stream=None):
+    _check(load().hase_step_graph(h, n_steps, _stream(stream)), h)
 
 
 def hase_obs_ptr(h):
@@ -292,6 +299,10 @@ class Engine:
 
     def step(self, n_steps=1):
         hase_step(self.h, n_steps, self.stream)
+
+    def step_graph(self, n_steps=1):
+        """The same steps replayed as one CUDA graph (captured on first use)."""
+        hase_step_graph(self.h, n_steps, self.stream)
 
     def reset(self):
         hase_reset(self.h, self.stream)

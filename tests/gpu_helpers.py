@@ -30,9 +30,16 @@ def compare_run(n_envs, seed, descs, n_steps, ring=None, flags=hase.HASE_EXPORT_
     lockstep; every slot still in the ring must match exactly."""
     ring = ring or n_steps + 1
     eng = hase.Engine(n_envs, seed, descs, ring, flags, env_id_base, **tuning)
-    for n in (launches or [n_steps]):
-        eng.step(n)
-    assert sum(launches or [n_steps]) == n_steps
+    total = 0
+    for item in (launches or [n_steps]):
+        # an int: hase_step; ("graph", n): the same steps as a replayed CUDA graph
+        if isinstance(item, tuple):
+            eng.step_graph(item[1])
+            total += item[1]
+        else:
+            eng.step(item)
+            total += item
+    assert total == n_steps
     got = engine_outputs(eng)
     unpacked = bool(flags & hase.HASE_EXPORT_UNPACKED)
     w = oracle.World(n_envs, seed, descs, env_id_base=env_id_base)

@@ -64,6 +64,26 @@ def test_launch_configurations_agree(tuning):
     compare_run(40, 11, W.uneven_descs(40, 5), 90, **tuning)
 
 
+def test_graph_replays_match_oracle():
+    c = W.ten1k()
+    descs = [dict(c["descs"][0], cap=45)]
+    # one graph replayed four times, mixed with plain launches and a second graph
+    compare_run(50, c["seed"], descs, 180, launches=[("graph", 32), ("graph", 32), 5, ("graph", 32),
+                                                     ("graph", 32), ("graph", 47)])
+    compare_run(40, 11, W.uneven_descs(40, 5), 96, ring=10,
+                launches=[("graph", 24)] * 4, steps_per_launch=7)
+
+
+@pytest.mark.parametrize("cap", [32768, 65536, 98304])
+def test_shared_memory_caps_agree(cap):
+    compare_run(60, 12, W.uneven_descs(60, 6), 70, smem_cap=cap)
+
+
+def test_shared_memory_cap_too_small_rejected():
+    with pytest.raises(hase.HaseError):
+        hase.Engine(2, 1, [W.env_desc(64, 16, 8, 4, 4, 10, "0.2")], 8, smem_cap=16384)
+
+
 def test_ring_wraparound_and_split_launches():
     c = W.ten1k()
     compare_run(64, c["seed"], c["descs"], 300, ring=7, launches=[1, 2, 97, 200])
