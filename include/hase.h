@@ -78,6 +78,13 @@ typedef enum hase_status {
 /* Configuration flags. */
 #define HASE_EXPORT_ACTIONS 1u  /* keep the actions of every step          */
 #define HASE_EXPORT_UNPACKED 2u /* also write the uint8 unpacked obs       */
+#define HASE_ASYNC_CREATE 4u    /* hase_create does not wait for the world   */
+                                /* generation; a failed start-cell draw is   */
+                                /* reported by hase_sync and hase_digest     */
+#define HASE_POOL_ALLOC 8u      /* buffers from the device's stream-ordered  */
+                                /* pool (allocated on the create stream,     */
+                                /* returned by hase_destroy on the stream of */
+                                /* the handle's last call)                   */
 
 /* Observation emitters (hase_env_desc.obs_teams). */
 #define HASE_OBS_SEEKERS 1u
@@ -131,6 +138,16 @@ typedef struct hase_layout {
 
 typedef struct hase_handle hase_handle;
 
+/* Summary of a run of steps (hase_digest), all exact integers. */
+typedef struct hase_digest_out {
+    uint64_t digest;     /* sum mod 2^64 over steps s and obs words j of     */
+                         /* splitmix64(obs[s][j] ^ (s * obs_words + j))     */
+    uint64_t episodes;   /* done bits over the steps and envs                */
+    int64_t reward_sum;  /* rewards over the steps and agents                */
+    uint32_t gen_error;  /* nonzero: the world generation failed             */
+    uint32_t pad;
+} hase_digest_out;
+
 /* Create a batch on the current CUDA device: validates the configuration,
  * allocates every buffer, generates the worlds (a0) and writes the step -1
  * observation, all on `stream` (a cudaStream_t, NULL = legacy default).
@@ -160,6 +177,16 @@ hase_status hase_layout_get(hase_handle *h, hase_layout *out);
  * must not itself run inside another stream capture.  Graphs are freed by
  * hase_destroy.  Not in the paper: a launch-overhead device of this engine. */
 hase_status hase_step_graph(hase_handle *h, uint32_t n_steps, void *stream);
+
+/* Reduce the outputs of the last n_steps steps (1 <= n_steps <= ring_steps,
+ * n_steps <= steps taken), s = 0 being the oldest of them, into *out
+ * (device memory, overwritten) and, when agent_rew is not NULL, the
+ * per-agent reward sums into agent_rew (device, int64 [agents]).  Enqueued
+ * on `stream`; uses the handle's own scratch, so two calls on one handle must
+ * not overlap.  splitmix64 is the output function of Steele, Lea and Flood
+ * (OOPSLA 2014).  Not in the paper: a result summary for serving and tests. */
+hase_status hase_digest(hase_handle *h, uint32_t n_steps, hase_digest_out *out, int64_t *agent_rew,
+                        void *stream);
 
 /* Steps taken since create / reset. */
 hase_status hase_step_count(hase_handle *h, uint64_t *t);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libhase.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["hase_kernels.cu", "hase_api.cu"]
+SOURCES = ["hase_kernels.cu", "hase_api.cu", "hase_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]
@@ -32,8 +32,9 @@ def source_digest():
         h.update(f.encode())
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
-    with open(os.path.join(ROOT, "include", "hase.h"), "rb") as fh:
-        h.update(fh.read())
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        with open(os.path.join(ROOT, "include", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -54,7 +55,7 @@ def _stale(target, deps):
 def build(force=False, verbose=False, ptxas_info=False):
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "hase.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

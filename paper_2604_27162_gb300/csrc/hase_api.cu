@@ -22,6 +22,11 @@ cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* po
 cudaError_t launch_step(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
                         cudaStream_t st);
 cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st);
+cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
+                          uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
+                          uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
+                          int64_t* agent_rew, cudaStream_t st);
+constexpr uint32_t kDigestBlocks = 256;  // partial sums of the digest's first pass
 cudaError_t prepare_step(uint32_t smem);
 }  // namespace hase
 
@@ -41,6 +46,8 @@ struct hase_handle {
     uint32_t smem_budget = kSmemBudget;
     uint64_t t = 0;
     uint64_t* d_clock = nullptr;  // steps enqueued before the running launch
+    uint64_t* d_scratch = nullptr;  // digest partial sums [kDigestBlocks][3]
+    cudaStream_t last_stream = nullptr;  // stream of the latest call (pool frees)
     cudaStream_t cap_stream = nullptr;
     std::map<uint32_t, cudaGraphExec_t> graphs;
     // device memory
@@ -90,9 +97,15 @@ static hase_status cuda_fail(hase_handle* h, cudaError_t e, const char* what) {
 static void free_all(hase_handle* h) {
     void* ptrs[] = {h->d_env, h->d_est,  h->d_pos, h->d_start, h->d_rows, h->d_groups,
                     h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr, h->d_env_list,
-                    h->d_clock};
+                    h->d_clock, h->d_scratch};
+    const bool pool = h->flags & HASE_POOL_ALLOC;
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) {
+            if (pool)
+                cudaFreeAsync(p, h->last_stream);
+            else
+                cudaFree(p);
+        }
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
     h->graphs.clear();
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -213,7 +226,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if (cfg->ring_steps < 1) return fail(nullptr, HASE_EINVAL, "ring_steps must be >= 1");
     if ((uint64_t)cfg->env_id_base + cfg->n_envs > 0x100000000ull)
         return fail(nullptr, HASE_EINVAL, "env ids exceed 32 bits");
-    if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED))
+    if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED | HASE_ASYNC_CREATE | HASE_POOL_ALLOC))
         return fail(nullptr, HASE_EINVAL, "unknown flags 0x%x", cfg->flags);
     if (cfg->chunk_steps != 0 && (cfg->chunk_steps < 1 || cfg->chunk_steps > (uint32_t)kMaxChunk))
         return fail(nullptr, HASE_EINVAL, "chunk_steps outside 1..%d", kMaxChunk);
@@ -309,7 +322,21 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     }
     h->threads = 32 * (h->n_dyn + h->emit_warps);
 
+    h->last_stream = st;
+    if (h->flags & HASE_POOL_ALLOC) {
+        // keep freed pool memory cached for the next handles (once per device)
+        static int pool_ready[64] = {0};
+        if (h->device >= 0 && h->device < 64 && !pool_ready[h->device]) {
+            cudaMemPool_t mp;
+            if (cudaDeviceGetDefaultMemPool(&mp, h->device) == cudaSuccess) {
+                uint64_t thr = ~0ull;
+                cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
+            }
+            pool_ready[h->device] = 1;
+        }
+    }
     auto alloc = [&](void** p, size_t bytes) -> cudaError_t {
+        if (h->flags & HASE_POOL_ALLOC) return cudaMallocAsync(p, bytes ? bytes : 16, st);
         return cudaMalloc(p, bytes ? bytes : 16);
     };
     const uint64_t R = h->ring;
@@ -331,6 +358,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     HASE_ALLOC(h->d_err, 4);
     HASE_ALLOC(h->d_thr, 4 * h->n_envs);
     HASE_ALLOC(h->d_clock, 8);
+    HASE_ALLOC(h->d_scratch, 8 * 3 * kDigestBlocks);
 #undef HASE_ALLOC
     if (ce != cudaSuccess) {
         hase_status s = cuda_fail(nullptr, ce, "cudaMalloc");
@@ -375,6 +403,10 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
                                    h->d_unp ? h->d_unp + last * h->unp_bytes : nullptr, st),
                     "observe")) != HASE_OK)
         return s;
+    if (h->flags & HASE_ASYNC_CREATE) {  // the generation flag is read by hase_sync / hase_digest
+        *out = h;
+        return HASE_OK;
+    }
     uint32_t herr = 0;
     if ((s = finish(cudaMemcpyAsync(&herr, h->d_err, 4, cudaMemcpyDeviceToHost, st), "copy err")) != HASE_OK)
         return s;
@@ -391,6 +423,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
 hase_status hase_reset(hase_handle* h, void* stream) {
     if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
     cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
     const uint64_t last = h->ring - 1;
     HASE_CUDA(h, cudaMemcpyAsync(h->d_pos, h->d_start, 2 * h->agents, cudaMemcpyDeviceToDevice, st));
     HASE_CUDA(h, cudaMemsetAsync(h->d_est, 0, sizeof(EnvState) * h->n_envs, st));
@@ -455,6 +488,7 @@ hase_status hase_step(hase_handle* h, uint32_t n_steps, void* stream) {
     if (n_steps == 0) return HASE_OK;
     hase_status s = check_steps(h, n_steps);
     if (s != HASE_OK) return s;
+    h->last_stream = (cudaStream_t)stream;
     s = enqueue_steps(h, n_steps, (cudaStream_t)stream);
     if (s != HASE_OK) return s;
     h->t += n_steps;
@@ -484,6 +518,7 @@ hase_status hase_step_graph(hase_handle* h, uint32_t n_steps, void* stream) {
         HASE_CUDA(h, ie);
         it = h->graphs.emplace(n_steps, exec).first;
     }
+    h->last_stream = (cudaStream_t)stream;
     HASE_CUDA(h, cudaGraphLaunch(it->second, (cudaStream_t)stream));
     h->t += n_steps;
     return HASE_OK;
@@ -615,6 +650,27 @@ hase_status hase_get_world(hase_handle* h, uint32_t e, uint8_t* grid, int32_t* s
 hase_status hase_sync(hase_handle* h) {
     if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
     HASE_CUDA(h, cudaDeviceSynchronize());
+    if (h->flags & HASE_ASYNC_CREATE) {
+        uint32_t herr = 0;
+        HASE_CUDA(h, cudaMemcpy(&herr, h->d_err, 4, cudaMemcpyDeviceToHost));
+        if (herr) return fail(h, HASE_EINVAL, "start-cell draw did not terminate");
+    }
+    return HASE_OK;
+}
+
+hase_status hase_digest(hase_handle* h, uint32_t n_steps, hase_digest_out* out, int64_t* agent_rew,
+                        void* stream) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (!out) return fail(h, HASE_EINVAL, "out is NULL");
+    if (n_steps < 1 || n_steps > h->ring || n_steps > h->t)
+        return fail(h, HASE_EINVAL, "n_steps must be in 1..min(ring_steps, steps taken)");
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    const uint64_t total = (uint64_t)n_steps * std::max<uint64_t>(h->obs_words, h->agents);
+    const uint32_t n_part = (uint32_t)std::min<uint64_t>(kDigestBlocks, std::max<uint64_t>(1, (total + 255) / 256));
+    HASE_CUDA(h, launch_digest(h->d_obs, h->d_done, h->d_rew, h->obs_words, h->n_envs, h->agents, h->ring,
+                               h->t - n_steps, n_steps, h->d_scratch, n_part, h->d_err,
+                               reinterpret_cast<uint64_t*>(out), agent_rew, st));
     return HASE_OK;
 }
 

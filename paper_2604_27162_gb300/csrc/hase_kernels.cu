@@ -23,6 +23,8 @@
 //                   parallel over steps.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "hase_internal.cuh"
 
 namespace hase {
@@ -1025,6 +1027,125 @@ cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* po
                            const uint64_t* rows, uint64_t* obs, uint8_t* unp, cudaStream_t st) {
     if (n_envs == 0) return cudaSuccess;
     observe_kernel<<<n_envs, 32, 0, st>>>(env, n_envs, pos, rows, obs, unp);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// Run digest: order-independent sums (mod 2^64) over the ring slots of the
+// last n steps.  Pass 1: every block reduces a grid-stride share of the obs
+// words, done bytes and rewards into scratch[block] (three words); pass 2: one
+// block adds the partials.  A third kernel gives per-agent reward sums.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    T s = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+// Flattened (step, item) walk: start at `i`, advance by the grid size.
+struct Walk {
+    uint64_t s, j, q, r;
+    __device__ Walk(uint64_t i, uint64_t items) {
+        s = i / items;
+        j = i - s * items;
+        const uint64_t g = (uint64_t)gridDim.x * blockDim.x;
+        q = g / items;
+        r = g - q * items;
+    }
+    __device__ void next(uint64_t items) {
+        j += r;
+        s += q;
+        if (j >= items) {
+            j -= items;
+            ++s;
+        }
+    }
+};
+
+__global__ void digest_partial_kernel(const uint64_t* obs, const uint8_t* done, const int32_t* rew,
+                                      uint64_t obs_words, uint64_t n_envs, uint64_t agents, uint32_t ring,
+                                      uint64_t first, uint32_t n_steps, uint64_t* scratch) {
+    __shared__ uint64_t red[32];
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t dig = 0, eps = 0, rs = 0;
+    if (obs_words) {
+        const uint64_t total = (uint64_t)n_steps * obs_words;
+        Walk w(i0, obs_words);
+        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(obs_words)) {
+            const uint64_t slot = (first + w.s) % ring;
+            dig += splitmix64(obs[slot * obs_words + w.j] ^ i);
+        }
+    }
+    {
+        const uint64_t total = (uint64_t)n_steps * n_envs;
+        Walk w(i0, n_envs);
+        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(n_envs))
+            eps += done[((first + w.s) % ring) * n_envs + w.j] & 1u;
+    }
+    {
+        const uint64_t total = (uint64_t)n_steps * agents;
+        Walk w(i0, agents);
+        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(agents))
+            rs += (uint64_t)(int64_t)rew[((first + w.s) % ring) * agents + w.j];
+    }
+    dig = block_sum(dig, red);
+    eps = block_sum(eps, red);
+    rs = block_sum(rs, red);
+    if (threadIdx.x == 0) {
+        scratch[3 * blockIdx.x + 0] = dig;
+        scratch[3 * blockIdx.x + 1] = eps;
+        scratch[3 * blockIdx.x + 2] = rs;
+    }
+}
+
+__global__ void digest_final_kernel(const uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out) {
+    __shared__ uint64_t red[32];
+    uint64_t v[3] = {0, 0, 0};
+    for (uint32_t b = threadIdx.x; b < n_part; b += blockDim.x)
+        for (int k = 0; k < 3; ++k) v[k] += scratch[3 * b + k];
+    for (int k = 0; k < 3; ++k) v[k] = block_sum(v[k], red);
+    if (threadIdx.x == 0) {
+        out[0] = v[0];
+        out[1] = v[1];
+        out[2] = v[2];
+        out[3] = err ? (uint64_t)*err : 0ull;
+    }
+}
+
+__global__ void agent_reward_kernel(const int32_t* rew, uint64_t agents, uint32_t ring, uint64_t first,
+                                    uint32_t n_steps, int64_t* agent_rew) {
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < agents;
+         a += (uint64_t)gridDim.x * blockDim.x) {
+        int64_t s = 0;
+        for (uint32_t k = 0; k < n_steps; ++k) s += rew[((first + k) % ring) * agents + a];
+        agent_rew[a] = s;
+    }
+}
+
+cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
+                          uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
+                          uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
+                          int64_t* agent_rew, cudaStream_t st) {
+    digest_partial_kernel<<<n_part, 256, 0, st>>>(obs, done, rew, obs_words, n_envs, agents, ring, first, n_steps,
+                                                  scratch);
+    digest_final_kernel<<<1, 256, 0, st>>>(scratch, n_part, err, out);
+    if (agent_rew && agents)
+        agent_reward_kernel<<<(uint32_t)std::min<uint64_t>((agents + 255) / 256, 1024), 256, 0, st>>>(
+            rew, agents, ring, first, n_steps, agent_rew);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_PKG, "libhase.so")
 HASE_OK, HASE_EINVAL, HASE_ENOMEM, HASE_ECUDA, HASE_ETIMEOUT, HASE_EBUSY, HASE_ESTATE = range(7)
 HASE_EXPORT_ACTIONS = 1
 HASE_EXPORT_UNPACKED = 2
+HASE_ASYNC_CREATE = 4
+HASE_POOL_ALLOC = 8
 HASE_OBS_SEEKERS = 1
 HASE_OBS_HIDERS = 2
 STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA",
@@ -29,9 +31,10 @@ STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA
 
 # Every symbol include/hase.h declares (the CPU tests check the export list).
 EXPORTS = [
-    "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
+    "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_digest", "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
     "hase_actions_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
     "hase_get_world", "hase_sync", "hase_launch_info", "hase_destroy", "hase_last_error",
+    "hase_request_bytes", "hase_serve",
 ]
 
 
@@ -60,6 +63,57 @@ class hase_config(C.Structure):
         ("emit_warps", C.c_uint32),
         ("max_group_envs", C.c_uint32),
         ("smem_cap", C.c_uint32),
+    ]
+
+
+class hase_digest_out(C.Structure):
+    _fields_ = [
+        ("digest", C.c_uint64),
+        ("episodes", C.c_uint64),
+        ("reward_sum", C.c_int64),
+        ("gen_error", C.c_uint32),
+        ("pad", C.c_uint32),
+    ]
+
+
+class hase_request(C.Structure):
+    _fields_ = [
+        ("arrival", C.c_double),
+        ("seed", C.c_uint64),
+        ("n_envs", C.c_uint32),
+        ("steps", C.c_uint32),
+        ("desc", hase_env_desc),
+    ]
+
+
+class hase_serve_config(C.Structure):
+    _fields_ = [
+        ("budget_bytes", C.c_uint64),
+        ("n_streams", C.c_uint32),
+        ("max_inflight", C.c_uint32),
+        ("time_scale", C.c_double),
+    ]
+
+
+class hase_request_result(C.Structure):
+    _fields_ = [
+        ("admitted", C.c_double),
+        ("finished", C.c_double),
+        ("digest", C.c_uint64),
+        ("episodes", C.c_uint64),
+        ("reward_sum", C.c_int64),
+        ("bytes", C.c_uint64),
+        ("status", C.c_uint32),
+        ("pad", C.c_uint32),
+    ]
+
+
+class hase_serve_stats(C.Structure):
+    _fields_ = [
+        ("makespan", C.c_double),
+        ("peak_bytes", C.c_uint64),
+        ("peak_inflight", C.c_uint32),
+        ("rejected", C.c_uint32),
     ]
 
 
@@ -94,6 +148,10 @@ def load(path=LIB_PATH):
     L.hase_reset.argtypes = [H, P]
     L.hase_step.argtypes = [H, u32, P]
     L.hase_step_graph.argtypes = [H, u32, P]
+    L.hase_digest.argtypes = [H, u32, P, P, P]
+    L.hase_request_bytes.argtypes = [C.POINTER(hase_request)]
+    L.hase_serve.argtypes = [C.POINTER(hase_request), u32, C.POINTER(hase_serve_config),
+                             C.POINTER(hase_request_result), C.POINTER(hase_serve_stats)]
     L.hase_obs_ptr.argtypes = [H, C.POINTER(P), C.POINTER(P)]
     L.hase_reward_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_done_ptr.argtypes = [H, C.POINTER(P)]
@@ -112,6 +170,7 @@ def load(path=LIB_PATH):
     for name in EXPORTS:
         if name not in ("hase_destroy", "hase_last_error"):
             getattr(L, name).restype = st
+    L.hase_request_bytes.restype = u64
     _lib = L
     return L
 
@@ -164,6 +223,45 @@ def hase_step(h, n_steps, stream=None):
 
 def hase_step_graph(h, n_steps, stream=None):
     _check(load().hase_step_graph(h, n_steps, _stream(stream)), h)
+
+
+def hase_digest(h, n_steps, out_ptr, agent_rew_ptr=None, stream=None):
+    """Enqueue the digest of the last n_steps steps into device memory at
+    out_ptr (a hase_digest_out) and, optionally, per-agent reward sums."""
+    _check(load().hase_digest(h, n_steps, C.c_void_p(out_ptr), C.c_void_p(agent_rew_ptr or 0),
+                              _stream(stream)), h)
+
+
+def _requests(reqs):
+    arr = (hase_request * max(1, len(reqs)))()
+    for i, r in enumerate(reqs):
+        arr[i].arrival = float(r["arrival"])
+        arr[i].seed = int(r["seed"]) & (2**64 - 1)
+        arr[i].n_envs = int(r["n_envs"])
+        arr[i].steps = int(r["steps"])
+        for k, _ in hase_env_desc._fields_:
+            setattr(arr[i].desc, k, int(r["desc"][k]))
+    return arr
+
+
+def hase_request_bytes(r):
+    return int(load().hase_request_bytes(C.byref(_requests([r])[0])))
+
+
+def hase_serve(reqs, budget_bytes, n_streams=16, max_inflight=1024, time_scale=1.0):
+    """Serve the request list (dicts with arrival, seed, n_envs, steps, desc)
+    and return (per-request result dicts, stats dict)."""
+    arr = _requests(reqs)
+    cfg = hase_serve_config(budget_bytes=int(budget_bytes), n_streams=n_streams, max_inflight=max_inflight,
+                            time_scale=float(time_scale))
+    res = (hase_request_result * max(1, len(reqs)))()
+    stats = hase_serve_stats()
+    status = load().hase_serve(arr, len(reqs), C.byref(cfg), res, C.byref(stats))
+    if status != HASE_OK:
+        raise HaseError(status, "hase_serve failed")
+    out = [{k: getattr(res[i], k) for k, _ in hase_request_result._fields_ if k != "pad"}
+           for i in range(len(reqs))]
+    return out, {k: getattr(stats, k) for k, _ in hase_serve_stats._fields_}
 
 
 def hase_obs_ptr(h):
@@ -299,6 +397,20 @@ class Engine:
 
     def step(self, n_steps=1):
         hase_step(self.h, n_steps, self.stream)
+
+    def digest(self, n_steps, per_agent=False):
+        """(digest, episodes, reward_sum, gen_error[, per-agent sums]) of the
+        last n_steps steps, reduced on the device."""
+        import numpy as np
+        import torch
+
+        out = torch.zeros(4, dtype=torch.int64, device="cuda")
+        ag = torch.zeros(self.layout["agents"], dtype=torch.int64, device="cuda") if per_agent else None
+        hase_digest(self.h, n_steps, out.data_ptr(), ag.data_ptr() if ag is not None else None, self.stream)
+        torch.cuda.synchronize()
+        v = out.cpu().numpy().view(np.uint64)
+        res = (int(v[0]), int(v[1]), int(np.int64(v[2])), int(v[3] & 0xffffffff))
+        return res + ((ag.cpu().numpy(),) if per_agent else ())
 
     def step_graph(self, n_steps=1):
         """The same steps replayed as one CUDA graph (captured on first use)."""

@@ -10,9 +10,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    text = open(os.path.join(ROOT, "include", "hase.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(hase_[a-z_]+)\s*\(", text)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if not f.endswith(".h"):
+            continue
+        text = open(os.path.join(inc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(hase_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol():
@@ -33,6 +39,11 @@ def test_binding_struct_sizes_match_header():
     assert ctypes.sizeof(hase.hase_env_desc) == 32
     assert ctypes.sizeof(hase.hase_config) == 56
     assert ctypes.sizeof(hase.hase_layout) == 56
+    assert ctypes.sizeof(hase.hase_digest_out) == 32
+    assert ctypes.sizeof(hase.hase_request) == 56
+    assert ctypes.sizeof(hase.hase_serve_config) == 24
+    assert ctypes.sizeof(hase.hase_request_result) == 56
+    assert ctypes.sizeof(hase.hase_serve_stats) == 24
 
 
 def test_missing_library_fails_loudly(tmp_path):
