@@ -26,7 +26,6 @@ cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_
                           uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
                           uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
                           int64_t* agent_rew, cudaStream_t st);
-constexpr uint32_t kDigestBlocks = 256;  // partial sums of the digest's first pass
 cudaError_t prepare_step(uint32_t smem);
 }  // namespace hase
 
@@ -658,6 +657,12 @@ hase_status hase_sync(hase_handle* h) {
     return HASE_OK;
 }
 
+// Partial-sum count of a digest over n_steps steps of h.
+static uint32_t digest_parts(const hase_handle* h, uint32_t n_steps) {
+    const uint64_t total = (uint64_t)n_steps * std::max<uint64_t>(h->obs_words, h->agents);
+    return (uint32_t)std::min<uint64_t>(kDigestBlocks, std::max<uint64_t>(1, (total + 255) / 256));
+}
+
 hase_status hase_digest(hase_handle* h, uint32_t n_steps, hase_digest_out* out, int64_t* agent_rew,
                         void* stream) {
     if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
@@ -666,8 +671,7 @@ hase_status hase_digest(hase_handle* h, uint32_t n_steps, hase_digest_out* out, 
         return fail(h, HASE_EINVAL, "n_steps must be in 1..min(ring_steps, steps taken)");
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;
-    const uint64_t total = (uint64_t)n_steps * std::max<uint64_t>(h->obs_words, h->agents);
-    const uint32_t n_part = (uint32_t)std::min<uint64_t>(kDigestBlocks, std::max<uint64_t>(1, (total + 255) / 256));
+    const uint32_t n_part = digest_parts(h, n_steps);
     HASE_CUDA(h, launch_digest(h->d_obs, h->d_done, h->d_rew, h->obs_words, h->n_envs, h->agents, h->ring,
                                h->t - n_steps, n_steps, h->d_scratch, n_part, h->d_err,
                                reinterpret_cast<uint64_t*>(out), agent_rew, st));

@@ -30,6 +30,7 @@ constexpr int kObsHiders = 2;         // obs_teams value: only hiders emit
 constexpr uint32_t kDoneBit = 0x8000u;
 constexpr uint32_t kOccBit = 0x80u;   // occupancy bit of the neighbour map
 constexpr uint32_t kSmemBudget = 216 * 1024;  // dynamic shared memory per CTA
+constexpr uint32_t kDigestBlocks = 256;        // partial sums of the digest's first pass
 
 __host__ __device__ inline uint32_t pack_xy(uint32_t x, uint32_t y) { return x | (y << 6); }
 __host__ __device__ inline uint32_t px(uint32_t p) { return p & 63u; }

@@ -1157,10 +1157,25 @@ cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Opt in to the shared memory of the largest CTA once, outside any capture.
+// Opt in, once per device and outside any capture, to all the dynamic shared
+// memory a block may have beside the kernel's static share.  One attribute
+// serves every handle (a per-handle value would cap the others' launches).
 cudaError_t prepare_step(uint32_t smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(step_kernel<512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static int done[64] = {0};
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, step_kernel<512, 1>);
+    if (e != cudaSuccess) return e;
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    if ((int)smem > dyn) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(step_kernel<512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+    return e;
 }
 
 template <int MAXT, int MINB>
