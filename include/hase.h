@@ -188,6 +188,20 @@ hase_status hase_step_graph(hase_handle *h, uint32_t n_steps, void *stream);
 hase_status hase_digest(hase_handle *h, uint32_t n_steps, hase_digest_out *out, int64_t *agent_rew,
                         void *stream);
 
+/* hase_digest without any allocation: the same reduction and results, with
+ * the partial sums of its first pass in a fixed device array of the library
+ * (at most 256 partial sums of 3 words, 6 KiB) instead of the handle's
+ * scratch.  Nothing in that array needs to start at zero (every slot read is
+ * written first in the same call).  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress, with the handle's device current);
+ * make it before any stream capture.  Calls that overlap in time -- on any
+ * handle or stream of the device -- race on the one array; serialise them.
+ * A digest that needs more partial sums than the array holds is rejected
+ * with HASE_EINVAL.  The paper has no counterpart: a scratch-free form of the
+ * run summary for callers that may not allocate. */
+hase_status hase_digest_noalloc(hase_handle *h, uint32_t n_steps, hase_digest_out *out, int64_t *agent_rew,
+                                void *stream);
+
 /* Steps taken since create / reset. */
 hase_status hase_step_count(hase_handle *h, uint64_t *t);
 

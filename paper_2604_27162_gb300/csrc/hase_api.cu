@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -26,6 +27,7 @@ cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_
                           uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
                           uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
                           int64_t* agent_rew, cudaStream_t st);
+cudaError_t digest_scratch_address(uint64_t** p, size_t* words);
 cudaError_t prepare_step(uint32_t smem);
 }  // namespace hase
 
@@ -661,6 +663,36 @@ hase_status hase_sync(hase_handle* h) {
 static uint32_t digest_parts(const hase_handle* h, uint32_t n_steps) {
     const uint64_t total = (uint64_t)n_steps * std::max<uint64_t>(h->obs_words, h->agents);
     return (uint32_t)std::min<uint64_t>(kDigestBlocks, std::max<uint64_t>(1, (total + 255) / 256));
+}
+
+hase_status hase_digest_noalloc(hase_handle* h, uint32_t n_steps, hase_digest_out* out, int64_t* agent_rew,
+                                void* stream) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (!out) return fail(h, HASE_EINVAL, "out is NULL");
+    if (n_steps < 1 || n_steps > h->ring || n_steps > h->t)
+        return fail(h, HASE_EINVAL, "n_steps must be in 1..min(ring_steps, steps taken)");
+    int dev = -1;
+    HASE_CUDA(h, cudaGetDevice(&dev));
+    if (dev != h->device) return fail(h, HASE_EINVAL, "the handle's device (%d) is not current (%d)", h->device, dev);
+    if (dev < 0 || dev >= 64) return fail(h, HASE_EINVAL, "device index %d beyond the scratch table", dev);
+    // the static scratch's address, looked up once per device with it current
+    static std::mutex mu;
+    static uint64_t* addr[64] = {nullptr};
+    static size_t words[64] = {0};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!addr[dev]) HASE_CUDA(h, digest_scratch_address(&addr[dev], &words[dev]));
+    }
+    const uint32_t n_part = digest_parts(h, n_steps);
+    if ((uint64_t)3 * n_part > words[dev])
+        return fail(h, HASE_EINVAL, "digest needs %u partial sums, the static scratch holds %zu", n_part,
+                    words[dev] / 3);
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    HASE_CUDA(h, launch_digest(h->d_obs, h->d_done, h->d_rew, h->obs_words, h->n_envs, h->agents, h->ring,
+                               h->t - n_steps, n_steps, addr[dev], n_part, h->d_err,
+                               reinterpret_cast<uint64_t*>(out), agent_rew, st));
+    return HASE_OK;
 }
 
 hase_status hase_digest(hase_handle* h, uint32_t n_steps, hase_digest_out* out, int64_t* agent_rew,

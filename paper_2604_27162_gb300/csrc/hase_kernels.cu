@@ -1136,6 +1136,16 @@ __global__ void agent_reward_kernel(const int32_t* rew, uint64_t agents, uint32_
     }
 }
 
+// Scratch of hase_digest_noalloc: the first pass's partial sums, 3 words per
+// block for at most kDigestBlocks blocks (6 KiB).  Pass 1 writes every slot
+// pass 2 reads, so nothing in it has to start at zero.
+static __device__ __align__(256) uint64_t g_digest_scratch[3 * kDigestBlocks];
+
+cudaError_t digest_scratch_address(uint64_t** p, size_t* words) {
+    *words = 3 * kDigestBlocks;
+    return cudaGetSymbolAddress(reinterpret_cast<void**>(p), g_digest_scratch);
+}
+
 cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
                           uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
                           uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,

@@ -31,7 +31,8 @@ STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA
 
 # Every symbol include/hase.h declares (the CPU tests check the export list).
 EXPORTS = [
-    "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_digest", "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
+    "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_digest", "hase_digest_noalloc",
+    "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
     "hase_actions_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
     "hase_get_world", "hase_sync", "hase_launch_info", "hase_destroy", "hase_last_error",
     "hase_request_bytes", "hase_serve",
@@ -149,6 +150,7 @@ def load(path=LIB_PATH):
     L.hase_step.argtypes = [H, u32, P]
     L.hase_step_graph.argtypes = [H, u32, P]
     L.hase_digest.argtypes = [H, u32, P, P, P]
+    L.hase_digest_noalloc.argtypes = [H, u32, P, P, P]
     L.hase_request_bytes.argtypes = [C.POINTER(hase_request)]
     L.hase_serve.argtypes = [C.POINTER(hase_request), u32, C.POINTER(hase_serve_config),
                              C.POINTER(hase_request_result), C.POINTER(hase_serve_stats)]
@@ -262,6 +264,12 @@ def hase_serve(reqs, budget_bytes, n_streams=16, max_inflight=1024, time_scale=1
     out = [{k: getattr(res[i], k) for k, _ in hase_request_result._fields_ if k != "pad"}
            for i in range(len(reqs))]
     return out, {k: getattr(stats, k) for k, _ in hase_serve_stats._fields_}
+
+
+def hase_digest_noalloc(h, n_steps, out_ptr, agent_rew_ptr=None, stream=None):
+    """hase_digest with the partial sums in the library's fixed scratch."""
+    _check(load().hase_digest_noalloc(h, n_steps, C.c_void_p(out_ptr), C.c_void_p(agent_rew_ptr or 0),
+                                      _stream(stream)), h)
 
 
 def hase_obs_ptr(h):
