@@ -113,7 +113,7 @@ typedef struct hase_config {
     uint32_t ring_steps;         /* output ring length in steps >= 1           */
     uint32_t flags;              /* HASE_EXPORT_*                              */
     uint32_t steps_per_launch;   /* steps fused per kernel launch, 0 = auto    */
-    uint32_t chunk_steps;        /* steps per on-chip chunk (1..32), 0 = auto  */
+    uint32_t chunk_steps;        /* steps per on-chip chunk (1..64), 0 = auto  */
     uint32_t emit_warps;         /* output warps per CTA (1..12), 0 = auto     */
     uint32_t max_group_envs;     /* envs packed per CTA (1..64), 0 = auto      */
     uint32_t smem_cap;           /* dynamic shared memory per CTA in bytes     */

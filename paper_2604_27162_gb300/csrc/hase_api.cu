@@ -248,7 +248,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     h->ring = cfg->ring_steps;
     h->flags = cfg->flags;
     h->seed = cfg->seed;
-    h->kc = cfg->chunk_steps ? cfg->chunk_steps : 32;
+    h->kc = cfg->chunk_steps ? cfg->chunk_steps : 64;
     // steps of one chunk are written concurrently: they must own distinct
     // ring slots, so a chunk never spans more steps than the ring holds
     h->kc = std::min(h->kc, h->ring);
@@ -309,15 +309,15 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         delete h;
         return fail(nullptr, HASE_EINVAL, "smem_cap %u is too small for one env of this batch", cfg->smem_cap);
     }
-    // emission warps.  Persistent regime (one CTA per SM): four when every
-    // group emits one (step, env) per thread (more warps only add store
-    // traffic in flight), else twelve; CTAs in waves: six.
+    // emission warps.  Persistent regime (one CTA per SM): nine when every
+    // group emits one (step, env) per thread (3 + 9 warps keep the 168
+    // register instantiation), else twelve; CTAs in waves: six.
     if (cfg->emit_warps) {
         h->emit_warps = cfg->emit_warps;
     } else if (h->groups.size() <= (size_t)n_sm) {
         bool fast = !(h->flags & HASE_EXPORT_UNPACKED);
         for (const Group& g : h->groups) fast = fast && fast_emission(h->env[h->env_list[g.list_first]]);
-        h->emit_warps = fast ? 4u : 12u;
+        h->emit_warps = fast ? 9u : 12u;
     } else {
         h->emit_warps = 6u;
     }

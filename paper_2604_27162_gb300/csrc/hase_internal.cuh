@@ -25,7 +25,7 @@ constexpr int kMaxAgents = 16;        // agents per env
 constexpr int kMaxGroupEnvs = 64;     // envs per CTA
 constexpr int kMaxGroupSlots = 128;   // agents per CTA (four dynamics warps)
 constexpr int kMaxDyn = 4;            // dynamics warps per CTA
-constexpr int kMaxChunk = 32;         // steps per on-chip chunk
+constexpr int kMaxChunk = 64;         // steps per on-chip chunk
 constexpr int kObsHiders = 2;         // obs_teams value: only hiders emit
 constexpr uint32_t kDoneBit = 0x8000u;
 constexpr uint32_t kOccBit = 0x80u;   // occupancy bit of the neighbour map
