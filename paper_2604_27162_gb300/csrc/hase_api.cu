@@ -315,7 +315,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if (cfg->emit_warps) {
         h->emit_warps = cfg->emit_warps;
     } else if (h->groups.size() <= (size_t)n_sm) {
-        bool fast = !(h->flags & HASE_EXPORT_UNPACKED);
+        bool fast = true;
         for (const Group& g : h->groups) fast = fast && fast_emission(h->env[h->env_list[g.list_first]]);
         h->emit_warps = fast ? 9u : 12u;
     } else {

@@ -395,6 +395,39 @@ struct TeamCtx {
     bool v16;             // the env's obs words start 16-byte aligned
 };
 
+// The unpacked export of one agent: bytes 0/1 of the three planes of DD
+// (<= 64) bits each, plane after plane.  Four bits at a time become one
+// 32-bit store: (b * 0x00204081) & 0x01010101 moves bit j of a 4-bit value b
+// to bit 0 of byte j.  Bytes before the first 4-byte boundary and after the
+// last one are stored singly.
+__device__ __forceinline__ void unpack_planes(uint8_t* u, uint64_t p0, uint64_t p1, uint64_t p2, uint32_t DD) {
+    const uint32_t n = 3u * DD;
+    uint32_t i = 0, p = 0, off = 0;  // byte i is bit `off` of plane p
+    auto plane = [&](uint32_t q) { return q == 0 ? p0 : (q == 1 ? p1 : p2); };
+    auto advance = [&](uint32_t k) {
+        off += k;
+        while (off >= DD) {
+            off -= DD;
+            ++p;
+        }
+    };
+    while (i < n && (reinterpret_cast<uintptr_t>(u + i) & 3u)) {
+        u[i] = (uint8_t)((plane(p) >> off) & 1u);
+        ++i;
+        advance(1);
+    }
+    for (; i + 4 <= n; i += 4) {
+        uint32_t b = (uint32_t)(plane(p) >> off);
+        if (off + 4 > DD) b = (b & ((1u << (DD - off)) - 1u)) | ((uint32_t)plane(p + 1) << (DD - off));
+        *reinterpret_cast<uint32_t*>(u + i) = ((b & 15u) * 0x00204081u) & 0x01010101u;
+        advance(4);
+    }
+    for (; i < n; ++i) {
+        u[i] = (uint8_t)((plane(p) >> off) & 1u);
+        advance(1);
+    }
+}
+
 // Observer a's three words (obstacle, ally, opponent planes); a seeker also
 // marks the hiders inside its window in seenf.
 struct Words3 {
@@ -452,15 +485,7 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
             uint64_t unused;
             obstacle_plane(T.rows, (int)T.rw, (int)xa, (int)ya, (int)R, w.o0, unused);
         }
-        if (T.unp) {
-            uint8_t* u = T.unp + T.slot[a].unp_rel;
-            const uint32_t DD = D * D;
-            for (uint32_t q = 0; q < DD; ++q) {
-                u[q] = (uint8_t)((w.o0 >> q) & 1u);
-                u[DD + q] = (uint8_t)((w.al >> q) & 1u);
-                u[2 * DD + q] = (uint8_t)((w.op >> q) & 1u);
-            }
-        }
+        if (T.unp) unpack_planes(T.unp + T.slot[a].unp_rel, w.o0, w.al, w.op, D * D);
     }
     return w;
 }
