@@ -524,6 +524,38 @@ def run_served(args):
     print(json.dumps(out))
 
 
+def run_reference_served(args, world):
+    """Reference arm of the served workload: the oracle runs requests of the
+    same stream one after another (digest of every step) for about a minute."""
+    import oracle
+
+    reqs = W.served_requests(duration=args.duration)
+    budget = 60.0
+    t0 = time.perf_counter()
+    done_env_steps = done_agent_steps = n = 0
+    for r in reqs:
+        w = oracle.World(r["n_envs"], r["seed"], [r["desc"]])
+        w.run_digest(r["steps"])
+        w.close()
+        n += 1
+        done_env_steps += r["n_envs"] * r["steps"]
+        done_agent_steps += r["n_envs"] * r["steps"] * r["desc"]["n_agents"]
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    value = done_env_steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": "env-steps/s", "value": value, "unit": "env-steps/s",
+        "agent_steps_per_s": done_agent_steps / dt, "n_gpus": world, "steps": 1, "warmup": 0,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic (Poisson request stream)",
+        "config": {"workload": "served", "requests_run": n},
+        "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "first %d requests of the stream, run back to back" % n},
+        "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
 def run_reference(args):
     """Reference arm: the oracle timed on the host cores, same metric."""
     import oracle
@@ -532,6 +564,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "served":
+        return run_reference_served(args, world)
     c = workload(args.workload)
     n = c["n_envs"]
     # bounded sample: each benchmark step runs a sample of the rollout, sized

@@ -68,12 +68,6 @@ __device__ __forceinline__ void set_bit(uint64_t& lo, uint64_t& hi, int bit) {
         hi |= 1ull << (bit - 64);
 }
 
-// packed-cell displacement of action a (x | y << 6): 1 N y-1, 2 S y+1,
-// 3 E x+1, 4 W x-1, 0 stay
-__device__ __forceinline__ int delta_of(uint32_t a) {
-    return a == 1u ? -64 : a == 2u ? 64 : a == 3u ? 1 : a == 4u ? -1 : 0;
-}
-
 // Obstacle plane (plane 0) of a window of radius r centred on (x, y) from
 // padded rows (rows point at padded row 0 of the env).
 __device__ __forceinline__ void obstacle_plane(const uint64_t* rows, int rw, int x, int y, int r,
@@ -113,8 +107,6 @@ __device__ __forceinline__ void team_planes_pairwise(int x, int y, int r, int a,
 // a1-a9 fused over n_steps steps.
 // --------------------------------------------------------------------------
 struct SlotRec {
-    uint32_t obs_rel;  // first obs word of this agent inside a slot, ~0u if it emits none
-    uint32_t rew_rel;  // reward / action index inside a slot
     uint32_t unp_rel;  // first unpacked byte inside a slot
     uint16_t p0;       // pristine start cell (CTA packing x | y << sh)
     uint8_t env;       // env index inside the group
@@ -128,8 +120,6 @@ struct CtaShared {
     SlotRec slot[kMaxGroupSlots];
     uint16_t p0[kMaxGroupSlots];  // pristine start cells (CTA packing)
     uint2 key[kMaxGroupSlots];     // Philox action counter words (agent, env id)
-    uint8_t team_list[2][kMaxGroupSlots];
-    uint32_t team_n[2];
 };
 
 __device__ __forceinline__ uint32_t to_cta(uint32_t p6, uint32_t sh) { return (p6 & 63u) | ((p6 >> 6) << sh); }
@@ -154,14 +144,13 @@ struct EmitCtx {
 };
 
 // ---------------------------------------------------------------------------
-// Segment emission (a5, a6, a9): one thread handles all agents of one
-// (step, env) with the positions in registers.  For every ordered pair
-// (a, b) it tests b against a's window (radius of a's team); the bit goes to
-// a's plane of b's team.  When a is a seeker and b a hider the same test is
-// the reward's "seen" test (seeker radius).  The agent count A (<= 16) and
-// the seeker count are runtime values shared by the group; the loops are
-// unrolled to 16 and skip past A (warp-uniform).  NW = 32-bit words per
-// plane: 2 when every window fits 64 bits, 3 with radius 4.
+// General emission (a5, a6, a9), for groups outside the one-thread form
+// below (windows over 64 bits, or seekers other than ceil(A/2)): one lane per
+// agent of a (step, env).  Each lane tests every other agent against its own
+// window (radius of its team) and sets the bit in the plane of that agent's
+// team; the reward's "seen" test (seeker radius) is combined over the
+// segment's lanes with warp ballots.  NW = 32-bit words per plane: 2 when
+// every window fits 64 bits, 3 with radius 4.
 // ---------------------------------------------------------------------------
 template <int NW>
 struct Plane {
@@ -364,8 +353,6 @@ __device__ __forceinline__ uint32_t shl_clamp(uint32_t v, uint32_t n) {
     return r;
 }
 
-// Byte q of w (q a compile-time constant after unrolling).
-__device__ __forceinline__ uint32_t byte_of(uint32_t w, int q) { return q == 3 ? w >> 24 : (w >> (8 * q)) & 0xffu; }
 
 // Segment emission with compile-time A (seekers NS = ceil(A/2)) and windows
 // of at most 64 bits (radius <= 3): one thread handles one (step, env), and
@@ -681,7 +668,6 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
 
     if (tid == 0) {
         int slot = 0;
-        H.team_n[0] = H.team_n[1] = 0;
         for (int i = 0; i < ne; ++i) {
             const uint32_t g = P.env_list[G.list_first + i];
             const EnvRT E = P.env[g];
@@ -693,19 +679,13 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                 SlotRec r;
                 r.env = (uint8_t)i;
                 r.agent = (uint8_t)a;
-                r.rew_rel = E.agent_off + a;
                 r.p0 = 0;
                 r.unp_rel = urel;
                 if (team_emits(E, t)) {
-                    const int ai = (E.obs_teams == kObsHiders) ? a - E.n_seekers : a;
-                    r.obs_rel = E.obs_off + (uint32_t)ai * 3u * E.wpp;
                     const int rr = team_radius(E, t);
                     urel += 3u * (2 * rr + 1) * (2 * rr + 1);
-                } else {
-                    r.obs_rel = ~0u;
                 }
                 H.slot[slot] = r;
-                H.team_list[t][H.team_n[t]++] = (uint8_t)slot;
                 ++slot;
             }
         }
