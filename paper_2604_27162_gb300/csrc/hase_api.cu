@@ -20,7 +20,7 @@ cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_en
                             cudaStream_t st);
 cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* pos,
                            const uint64_t* rows, uint64_t* obs, uint8_t* unp, cudaStream_t st);
-cudaError_t launch_step(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
+cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
                         cudaStream_t st);
 cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st);
 cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
@@ -45,6 +45,12 @@ struct hase_handle {
     uint64_t agents = 0, obs_words = 0, unp_bytes = 0, rows_words = 0;
     uint32_t smem = 0, threads = 0, kc = 16, emit_warps = 0, steps_per_launch = 0, n_dyn = 1;
     uint32_t smem_budget = kSmemBudget;
+    // launches of one step: the groups of each kernel family (contiguous)
+    struct Family {
+        int fam;
+        uint32_t first, count, smem, n_dyn, emit_warps, threads;
+    };
+    std::vector<Family> fams;
     uint64_t t = 0;
     uint64_t* d_clock = nullptr;  // steps enqueued before the running launch
     uint64_t* d_scratch = nullptr;  // digest partial sums [kDigestBlocks][3]
@@ -155,6 +161,8 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
     h->env_list.resize(E);
     for (uint32_t e = 0; e < E; ++e) h->env_list[e] = e;
     std::stable_sort(h->env_list.begin(), h->env_list.end(), [&](uint32_t a, uint32_t b) {
+        const int fa = family_of(h->env[a]), fb = family_of(h->env[b]);
+        if (fa != fb) return fa < fb;
         return shape_key(h->env[a]) < shape_key(h->env[b]);
     });
     uint32_t epc;
@@ -166,6 +174,7 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
         epc = kMaxGroupEnvs;  // bounded by one dynamics warp below
     const bool many = !max_envs_cfg && E > 16u * n_sm;
     h->groups.clear();
+    h->fams.clear();
     uint32_t smem_max = 0, dyn_max = 1;
     GroupPlan plan;
     std::vector<EnvRT> genv;
@@ -205,6 +214,13 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
         g.n_dyn = (uint8_t)plan.n_dyn;
         smem_max = std::max(smem_max, plan.total);
         dyn_max = std::max(dyn_max, plan.n_dyn);
+        const int fam = family_of(genv[0]);
+        if (h->fams.empty() || h->fams.back().fam != fam)
+            h->fams.push_back({fam, (uint32_t)h->groups.size(), 0u, 0u, 1u, 0u, 0u});
+        auto& F = h->fams.back();
+        F.count += 1;
+        F.smem = std::max(F.smem, plan.total);
+        F.n_dyn = std::max(F.n_dyn, plan.n_dyn);
         h->groups.push_back(g);
     }
     h->smem = smem_max;
@@ -309,19 +325,21 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         delete h;
         return fail(nullptr, HASE_EINVAL, "smem_cap %u is too small for one env of this batch", cfg->smem_cap);
     }
-    // emission warps.  Persistent regime (one CTA per SM): nine when every
-    // group emits one (step, env) per thread (3 + 9 warps keep the 168
-    // register instantiation), else twelve; CTAs in waves: six.
-    if (cfg->emit_warps) {
-        h->emit_warps = cfg->emit_warps;
-    } else if (h->groups.size() <= (size_t)n_sm) {
-        bool fast = true;
-        for (const Group& g : h->groups) fast = fast && fast_emission(h->env[h->env_list[g.list_first]]);
-        h->emit_warps = fast ? 9u : 12u;
-    } else {
-        h->emit_warps = 6u;
+    // emission warps per family.  Persistent regime (one CTA per SM): nine
+    // for the one-thread families (3 + 9 warps keep the 384-thread, 168
+    // register kernel), twelve for the general one; CTAs in waves: six.  The
+    // one-thread families run at most 12 warps a CTA in all.
+    const bool persistent = h->groups.size() <= (size_t)n_sm;
+    h->emit_warps = cfg->emit_warps;
+    h->threads = 0;
+    for (auto& F : h->fams) {
+        uint32_t M = cfg->emit_warps ? cfg->emit_warps : (!persistent ? 6u : (F.fam ? 9u : 12u));
+        if (F.fam) M = std::min(M, 12u - F.n_dyn);
+        F.emit_warps = M;
+        F.threads = 32 * (F.n_dyn + M);
+        h->threads = std::max(h->threads, F.threads);
     }
-    h->threads = 32 * (h->n_dyn + h->emit_warps);
+    if (!h->emit_warps && !h->fams.empty()) h->emit_warps = h->fams[0].emit_warps;
 
     h->last_stream = st;
     if (h->flags & HASE_POOL_ALLOC) {
@@ -467,11 +485,14 @@ static hase_status enqueue_steps(hase_handle* h, uint32_t n_steps, cudaStream_t 
         p.ring = h->ring;
         p.n_steps = n;
         p.kc = h->kc;
-        p.emit_warps = h->emit_warps;
-        p.n_dyn = h->n_dyn;
         p.key0 = (uint32_t)(h->seed & 0xffffffffu);
         p.key1 = (uint32_t)(h->seed >> 32);
-        HASE_CUDA(h, launch_step(p, (uint32_t)h->groups.size(), h->threads, h->smem, st));
+        for (const auto& F : h->fams) {
+            p.groups = h->d_groups + F.first;
+            p.emit_warps = F.emit_warps;
+            p.n_dyn = F.n_dyn;
+            HASE_CUDA(h, launch_step(F.fam, p, F.count, F.threads, F.smem, st));
+        }
         done += n;
     }
     HASE_CUDA(h, launch_advance(h->d_clock, n_steps, st));

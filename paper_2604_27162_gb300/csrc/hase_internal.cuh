@@ -100,6 +100,14 @@ __host__ __device__ inline bool fast_emission(const EnvRT& E) {
     return E.wpp == 1 && E.n_seekers == (E.n_agents + 1u) / 2u;
 }
 
+// Kernel families: family 0 runs the general (lane per agent) emission, family
+// f = 1..4 the one-thread emission for A in 4f-3 .. 4f; each group is launched
+// with the kernel of its family.
+constexpr int kFamilies = 5;
+__host__ __device__ inline int family_of(const EnvRT& E) {
+    return fast_emission(E) ? 1 + ((int)E.n_agents - 1) / 4 : 0;
+}
+
 // envs: the group's env constants in slot order.  Returns false when the
 // group does not fit the dynamics warps.
 __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uint16_t flags,

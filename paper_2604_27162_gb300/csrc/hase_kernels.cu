@@ -284,16 +284,20 @@ cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// The two step instantiations live in their own translation units.
-cudaError_t opt_in_step384(int optin);
-cudaError_t opt_in_step512(int optin);
-cudaError_t launch_step384(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
-                           cudaStream_t st);
-cudaError_t launch_step512(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
-                           cudaStream_t st);
+// The step kernel families live in their own translation units.
+#define HASE_FAMILY_DECL(f)                                                                            \
+    cudaError_t opt_in_f##f(int optin);                                                                \
+    cudaError_t launch_f##f(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem, \
+                            cudaStream_t st);
+HASE_FAMILY_DECL(0)
+HASE_FAMILY_DECL(1)
+HASE_FAMILY_DECL(2)
+HASE_FAMILY_DECL(3)
+HASE_FAMILY_DECL(4)
+#undef HASE_FAMILY_DECL
 
 // Opt in, once per device and outside any capture, to all the dynamic shared
-// memory a block may have beside the kernel's static share.  One attribute
+// memory a block may have beside each kernel's static share.  One attribute
 // per kernel serves every handle (a per-handle value would cap the others'
 // launches).
 cudaError_t prepare_step(uint32_t smem) {
@@ -305,20 +309,25 @@ cudaError_t prepare_step(uint32_t smem) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if ((int)smem + 8 * 1024 > optin) return cudaErrorInvalidValue;
-    if ((e = opt_in_step384(optin)) != cudaSuccess) return e;
-    if ((e = opt_in_step512(optin)) != cudaSuccess) return e;
+    cudaError_t (*opt[])(int) = {opt_in_f0, opt_in_f1, opt_in_f2, opt_in_f3, opt_in_f4};
+    for (auto f : opt)
+        if ((e = f(optin)) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = 1;
     return cudaSuccess;
 }
 
-// Up to 384 threads a CTA: up to 168 registers a thread; up to 512: 128
-// (the register file holds 64K).
-cudaError_t launch_step(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
+// One launch of the groups of one kernel family.
+cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
                         cudaStream_t st) {
     if (n_groups == 0 || p.n_steps == 0) return cudaSuccess;
-    if (threads <= 384) return launch_step384(p, n_groups, threads, smem, st);
-    if (threads <= 512) return launch_step512(p, n_groups, threads, smem, st);
-    return cudaErrorInvalidConfiguration;
+    switch (family) {
+        case 0: return launch_f0(p, n_groups, threads, smem, st);
+        case 1: return launch_f1(p, n_groups, threads, smem, st);
+        case 2: return launch_f2(p, n_groups, threads, smem, st);
+        case 3: return launch_f3(p, n_groups, threads, smem, st);
+        case 4: return launch_f4(p, n_groups, threads, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace hase

@@ -1,6 +1,6 @@
 // hase_step.cuh -- device code of the fused step kernel (a1-a9), included
-// by one translation unit per kernel instantiation (hase_step384.cu,
-// hase_step512.cu, compiled in parallel) and by hase_kernels.cu for the
+// by one translation unit per kernel family (hase_step_f0.cu ..
+// hase_step_f4.cu, compiled in parallel) and by hase_kernels.cu for the
 // shared helpers.
 //
 //   step_kernel     a1-a9 fused over K steps.  One CTA owns a group of envs
@@ -421,7 +421,7 @@ struct Words3 {
     uint64_t o0, al, op;
 };
 
-template <int A, bool TA>
+template <int A, bool TA, bool HI>
 __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32_t R, uint32_t D, uint32_t KR,
                                                  uint32_t C2, uint32_t KP, uint32_t centre, uint32_t centre_hi,
                                                  const uint32_t (&X4)[(A + 3) / 4], const uint32_t (&Y4)[(A + 3) / 4],
@@ -451,13 +451,14 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
             const int b = 4 * j + q;
             if (b >= A) continue;
             const uint32_t n = __byte_perm(n4, 0u, 0x4440u | (uint32_t)q);
-            const uint32_t m0 = shl_clamp(1u, n), m1 = shl_clamp(1u, n - 32u);
+            const uint32_t m0 = shl_clamp(1u, n);
+            const uint32_t m1 = HI ? shl_clamp(1u, n - 32u) : 0u;  // windows of over 32 bits only
             if ((b >= NS) == TA) {
                 al0 |= m0;
-                al1 |= m1;
+                if (HI) al1 |= m1;
             } else {
                 op0 |= m0;
-                op1 |= m1;
+                if (HI) op1 |= m1;
             }
         }
     }
@@ -485,7 +486,7 @@ __device__ __forceinline__ void st16(uint64_t* p, uint64_t a, uint64_t b) {
 // words of two consecutive observers leave as three 16-byte stores, and a
 // lone observer as one 16-byte and one 8-byte store; otherwise three 8-byte
 // stores per observer.
-template <int A, bool TA>
+template <int A, bool TA, bool HI>
 __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, const uint32_t (&X4)[(A + 3) / 4],
                                                const uint32_t (&Y4)[(A + 3) / 4], const uint32_t (&P4)[(A + 3) / 4],
                                                uint32_t (&seenf)[(A + 3) / 4]) {
@@ -498,13 +499,13 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
     constexpr int first = TA ? NS : 0, end = TA ? A : NS;
 #pragma unroll 1
     for (int a = first; a < end;) {
-        const Words3 p = observer_words<A, TA>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, seenf);
+        const Words3 p = observer_words<A, TA, HI>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, seenf);
         const int w = 3 * (a - T.ai0);
         uint64_t* o = T.ob + w;
         if (!T.emits) {
             ++a;
         } else if (T.v16 && !(w & 1) && a + 1 < end) {
-            const Words3 q = observer_words<A, TA>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4,
+            const Words3 q = observer_words<A, TA, HI>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4,
                                                    seenf);
             st16(o, p.o0, p.al);
             st16(o + 2, p.op, q.o0);
@@ -571,12 +572,18 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
     T.tbl = C.tbl + L.tbl_off[e][0];
     T.ai0 = 0;
     T.emits = emit_s;
-    emit_team_fast<A, false>(T, rs, X4, Y4, Ps, seenf);
+    if (Ds * Ds > 32u)
+        emit_team_fast<A, false, true>(T, rs, X4, Y4, Ps, seenf);
+    else
+        emit_team_fast<A, false, false>(T, rs, X4, Y4, Ps, seenf);
     if (A > 1 && emit_h) {
         T.tbl = C.tbl + L.tbl_off[e][1];
         T.ai0 = emit_s ? 0 : NS;
         T.emits = true;
-        emit_team_fast<A, true>(T, rh, X4, Y4, Ph, seenf);
+        if (Dh * Dh > 32u)
+            emit_team_fast<A, true, true>(T, rh, X4, Y4, Ph, seenf);
+        else
+            emit_team_fast<A, true, false>(T, rh, X4, Y4, Ph, seenf);
     }
     uint32_t seen = 0;
     if (done) {
@@ -626,26 +633,15 @@ __device__ __forceinline__ void emit_segments_fast(const StepParams& P, const Ct
     }
 }
 
+
+template <int FAM>
 __device__ __forceinline__ void emit_fast_dispatch(int A, const StepParams& P, const CtaShared& H,
                                                    const EmitCtx& C) {
-    switch (A) {
-        case 1: emit_segments_fast<1>(P, H, C); break;
-        case 2: emit_segments_fast<2>(P, H, C); break;
-        case 3: emit_segments_fast<3>(P, H, C); break;
-        case 4: emit_segments_fast<4>(P, H, C); break;
-        case 5: emit_segments_fast<5>(P, H, C); break;
-        case 6: emit_segments_fast<6>(P, H, C); break;
-        case 7: emit_segments_fast<7>(P, H, C); break;
-        case 8: emit_segments_fast<8>(P, H, C); break;
-        case 9: emit_segments_fast<9>(P, H, C); break;
-        case 10: emit_segments_fast<10>(P, H, C); break;
-        case 11: emit_segments_fast<11>(P, H, C); break;
-        case 12: emit_segments_fast<12>(P, H, C); break;
-        case 13: emit_segments_fast<13>(P, H, C); break;
-        case 14: emit_segments_fast<14>(P, H, C); break;
-        case 15: emit_segments_fast<15>(P, H, C); break;
-        default: emit_segments_fast<16>(P, H, C); break;
-    }
+    constexpr int a0 = 4 * FAM - 3;
+    if (A == a0) emit_segments_fast<a0>(P, H, C);
+    else if (A == a0 + 1) emit_segments_fast<a0 + 1>(P, H, C);
+    else if (A == a0 + 2) emit_segments_fast<a0 + 2>(P, H, C);
+    else emit_segments_fast<a0 + 3>(P, H, C);
 }
 
 // Per-cell shared state of the dynamics: a claim word (byte a-1 holds the
@@ -654,7 +650,7 @@ __device__ __forceinline__ void emit_fast_dispatch(int A, const StepParams& P, c
 // bit 7: occupied).
 constexpr uint32_t kNoClaims = 0xffffffffu;
 
-template <int MAXT, int MINB>
+template <int MAXT, int MINB, int FAM>
 __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
     extern __shared__ __align__(16) uint8_t sm[];
     __shared__ CtaShared H;
@@ -928,9 +924,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
     const int worker = tid - n_dyn * 32;
     const int n_workers = M * 32;
     const bool wide = H.env[0].wpp == 2;  // the group shares its radii
-    // one thread per (step, env) when the seekers are ceil(A/2) and every
-    // window fits one word; else one lane per agent
-    const bool fast = fast_emission(H.env[0]);
+    (void)wide;
     for (uint32_t c = 0; c <= n_chunks; ++c) {
         if (c >= 1) {
             const uint32_t cp = c - 1;
@@ -943,12 +937,14 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             C.base_slot = (uint32_t)((T0 + (uint64_t)cp * kc) % P.ring);
             C.worker = worker;
             C.n_workers = n_workers;
-            if (fast)
-                emit_fast_dispatch(H.env[0].n_agents, P, H, C);
-            else if (wide)
-                emit_chunk<3>(P, H, C, warp - n_dyn, M, lane);
-            else
-                emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
+            if constexpr (FAM > 0) {
+                emit_fast_dispatch<FAM>(H.env[0].n_agents, P, H, C);
+            } else {
+                if (wide)
+                    emit_chunk<3>(P, H, C, warp - n_dyn, M, lane);
+                else
+                    emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
+            }
         }
         // a1 for chunk c + 1
         if (c + 1 < n_chunks) draw_actions(c + 1, worker, n_workers);
