@@ -94,18 +94,20 @@ struct GroupPlan {
     uint16_t flags;
 };
 
-// One thread emits a whole (step, env) when every window fits one word and
-// the seekers are the first ceil(A / 2) agents.
+// One thread emits a whole (step, env) when the seekers are the first
+// ceil(A / 2) agents (windows of up to two words a plane).
 __host__ __device__ inline bool fast_emission(const EnvRT& E) {
-    return E.wpp == 1 && E.n_seekers == (E.n_agents + 1u) / 2u;
+    return E.wpp <= 2 && E.n_seekers == (E.n_agents + 1u) / 2u;
 }
 
-// Kernel families: family 0 runs the general (lane per agent) emission, family
-// f = 1..4 the one-thread emission for A in 4f-3 .. 4f; each group is launched
-// with the kernel of its family.
-constexpr int kFamilies = 5;
+// Kernel families: family 0 runs the general (lane per agent) emission;
+// families 1..4 the one-thread emission for A in 1-4, 5-8, 9-12, 13-16 with
+// one word a plane, families 5..8 the same with two words a plane (radius 4).
+// Each group is launched with the kernel of its family.
+constexpr int kFamilies = 9;
 __host__ __device__ inline int family_of(const EnvRT& E) {
-    return fast_emission(E) ? 1 + ((int)E.n_agents - 1) / 4 : 0;
+    if (!fast_emission(E)) return 0;
+    return (E.wpp == 2 ? 5 : 1) + ((int)E.n_agents - 1) / 4;
 }
 
 // envs: the group's env constants in slot order.  Returns false when the

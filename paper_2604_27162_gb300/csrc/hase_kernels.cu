@@ -294,6 +294,10 @@ HASE_FAMILY_DECL(1)
 HASE_FAMILY_DECL(2)
 HASE_FAMILY_DECL(3)
 HASE_FAMILY_DECL(4)
+HASE_FAMILY_DECL(5)
+HASE_FAMILY_DECL(6)
+HASE_FAMILY_DECL(7)
+HASE_FAMILY_DECL(8)
 #undef HASE_FAMILY_DECL
 
 // Opt in, once per device and outside any capture, to all the dynamic shared
@@ -309,7 +313,8 @@ cudaError_t prepare_step(uint32_t smem) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if ((int)smem + 8 * 1024 > optin) return cudaErrorInvalidValue;
-    cudaError_t (*opt[])(int) = {opt_in_f0, opt_in_f1, opt_in_f2, opt_in_f3, opt_in_f4};
+    cudaError_t (*opt[])(int) = {opt_in_f0, opt_in_f1, opt_in_f2, opt_in_f3, opt_in_f4,
+                                 opt_in_f5, opt_in_f6, opt_in_f7, opt_in_f8};
     for (auto f : opt)
         if ((e = f(optin)) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = 1;
@@ -326,6 +331,10 @@ cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint
         case 2: return launch_f2(p, n_groups, threads, smem, st);
         case 3: return launch_f3(p, n_groups, threads, smem, st);
         case 4: return launch_f4(p, n_groups, threads, smem, st);
+        case 5: return launch_f5(p, n_groups, threads, smem, st);
+        case 6: return launch_f6(p, n_groups, threads, smem, st);
+        case 7: return launch_f7(p, n_groups, threads, smem, st);
+        case 8: return launch_f8(p, n_groups, threads, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -415,24 +415,37 @@ __device__ __forceinline__ void unpack_planes(uint8_t* u, uint64_t p0, uint64_t 
     }
 }
 
-// Observer a's three words (obstacle, ally, opponent planes); a seeker also
-// marks the hiders inside its window in seenf.
+// Observer a's three planes (obstacle, ally, opponent): bits 0-63 and, with
+// radius-4 windows (W2), bits 64-80; a seeker also marks the hiders inside its
+// window in seenf.
 struct Words3 {
     uint64_t o0, al, op;
+    uint32_t o0h, alh, oph;
 };
 
-template <int A, bool TA, bool HI>
+// The unpacked export of windows over 64 bits (radius 4): byte by byte.
+__device__ __forceinline__ void unpack_planes_wide(uint8_t* u, const Words3& w, uint32_t DD) {
+    for (uint32_t q = 0; q < DD; ++q) {
+        const bool lo = q < 64u;
+        u[q] = (uint8_t)(lo ? (w.o0 >> q) & 1u : (w.o0h >> (q - 64u)) & 1u);
+        u[DD + q] = (uint8_t)(lo ? (w.al >> q) & 1u : (w.alh >> (q - 64u)) & 1u);
+        u[2 * DD + q] = (uint8_t)(lo ? (w.op >> q) & 1u : (w.oph >> (q - 64u)) & 1u);
+    }
+}
+
+template <int A, bool TA, bool HI, bool W2>
 __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32_t R, uint32_t D, uint32_t KR,
                                                  uint32_t C2, uint32_t KP, uint32_t centre, uint32_t centre_hi,
                                                  const uint32_t (&X4)[(A + 3) / 4], const uint32_t (&Y4)[(A + 3) / 4],
-                                                 const uint32_t (&P4)[(A + 3) / 4], uint32_t (&seenf)[(A + 3) / 4]) {
+                                                 const uint32_t (&P4)[(A + 3) / 4], const uint32_t (&P8)[(A + 3) / 4],
+                                                 uint32_t (&seenf)[(A + 3) / 4]) {
     constexpr int NS = (A + 1) / 2, NW = (A + 3) / 4;
     const uint32_t v = T.src[a] & 0x0fffu;
     const uint32_t xa = v & T.xmask, ya = v >> T.sh;
     const uint32_t Kx = KR - xa * 0x01010101u, Ky = KR - ya * 0x01010101u;
     const uint32_t Kp = ((KP - (ya * D + xa)) & 0xffu) * 0x01010101u;
-    const uint32_t Kp7 = Kp & 0x7f7f7f7fu;
-    uint32_t al0 = 0, al1 = 0, op0 = 0, op1 = 0;
+    const uint32_t Kp7 = Kp & 0x7f7f7f7fu, Kp8 = Kp & 0x80808080u;
+    uint32_t al0 = 0, al1 = 0, op0 = 0, op1 = 0, al2 = 0, op2 = 0;
 #pragma unroll
     for (int j = 0; j < NW; ++j) {
         const uint32_t vx = X4[j] + Kx, vy = Y4[j] + Ky;
@@ -445,7 +458,8 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
                 if (4 * j + q >= NS && 4 * j + q < A) hid |= 0x80u << (8 * q);
             seenf[j] |= ~fail & hid;
         }
-        const uint32_t n4 = (((P4[j] & 0x7f7f7f7fu) + Kp7) ^ ((P4[j] ^ Kp) & 0x80808080u)) | fail;
+        // P4[j] holds the bytes' low 7 bits, P8[j] their bit 7 (split once per segment)
+        const uint32_t n4 = ((P4[j] + Kp7) ^ (P8[j] ^ Kp8)) | fail;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int b = 4 * j + q;
@@ -453,27 +467,45 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
             const uint32_t n = __byte_perm(n4, 0u, 0x4440u | (uint32_t)q);
             const uint32_t m0 = shl_clamp(1u, n);
             const uint32_t m1 = HI ? shl_clamp(1u, n - 32u) : 0u;  // windows of over 32 bits only
+            const uint32_t m2 = W2 ? shl_clamp(1u, n - 64u) : 0u;  // windows of over 64 bits only
             if ((b >= NS) == TA) {
                 al0 |= m0;
                 if (HI) al1 |= m1;
+                if (W2) al2 |= m2;
             } else {
                 op0 |= m0;
                 if (HI) op1 |= m1;
+                if (W2) op2 |= m2;
             }
         }
     }
     Words3 w;
     w.al = (uint64_t)(al0 & centre) | ((uint64_t)(al1 & centre_hi) << 32);
     w.op = (uint64_t)op0 | ((uint64_t)op1 << 32);
+    w.alh = al2;  // the centre bit (R D + R <= 40) is never in the high word
+    w.oph = op2;
     w.o0 = 0;
+    w.o0h = 0;
     if (T.emits) {  // a5 obstacle plane
         if (T.use_table) {
-            w.o0 = T.tbl[ya * T.side + xa];
+            if (W2 && R == 4u) {  // two table words a cell
+                const uint64_t* c = T.tbl + 2u * (ya * T.side + xa);
+                w.o0 = c[0];
+                w.o0h = (uint32_t)c[1];
+            } else {
+                w.o0 = T.tbl[ya * T.side + xa];
+            }
         } else {
-            uint64_t unused;
-            obstacle_plane(T.rows, (int)T.rw, (int)xa, (int)ya, (int)R, w.o0, unused);
+            uint64_t hi;
+            obstacle_plane(T.rows, (int)T.rw, (int)xa, (int)ya, (int)R, w.o0, hi);
+            w.o0h = (uint32_t)hi;
         }
-        if (T.unp) unpack_planes(T.unp + T.slot[a].unp_rel, w.o0, w.al, w.op, D * D);
+        if (T.unp) {
+            if (W2)
+                unpack_planes_wide(T.unp + T.slot[a].unp_rel, w, D * D);
+            else
+                unpack_planes(T.unp + T.slot[a].unp_rel, w.o0, w.al, w.op, D * D);
+        }
     }
     return w;
 }
@@ -486,10 +518,10 @@ __device__ __forceinline__ void st16(uint64_t* p, uint64_t a, uint64_t b) {
 // words of two consecutive observers leave as three 16-byte stores, and a
 // lone observer as one 16-byte and one 8-byte store; otherwise three 8-byte
 // stores per observer.
-template <int A, bool TA, bool HI>
+template <int A, bool TA, bool HI, bool W2>
 __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, const uint32_t (&X4)[(A + 3) / 4],
                                                const uint32_t (&Y4)[(A + 3) / 4], const uint32_t (&P4)[(A + 3) / 4],
-                                               uint32_t (&seenf)[(A + 3) / 4]) {
+                                               const uint32_t (&P8)[(A + 3) / 4], uint32_t (&seenf)[(A + 3) / 4]) {
     constexpr int NS = (A + 1) / 2;
     const uint32_t D = 2u * R + 1u;
     const uint32_t KR = (0x80u + R) * 0x01010101u;
@@ -497,16 +529,38 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
     const uint32_t KP = R * D + R;
     const uint32_t centre = ~shl_clamp(1u, KP), centre_hi = ~shl_clamp(1u, KP - 32u);
     constexpr int first = TA ? NS : 0, end = TA ? A : NS;
+    if (W2) {  // two words a plane: six words an observer, three 16-byte stores
+#pragma unroll 1
+        for (int a = first; a < end; ++a) {
+            const Words3 p =
+                observer_words<A, TA, HI, W2>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
+            if (!T.emits) continue;
+            uint64_t* o = T.ob + 6 * (a - T.ai0);
+            if (T.v16) {
+                st16(o, p.o0, p.o0h);
+                st16(o + 2, p.al, p.alh);
+                st16(o + 4, p.op, p.oph);
+            } else {
+                o[0] = p.o0;
+                o[1] = p.o0h;
+                o[2] = p.al;
+                o[3] = p.alh;
+                o[4] = p.op;
+                o[5] = p.oph;
+            }
+        }
+        return;
+    }
 #pragma unroll 1
     for (int a = first; a < end;) {
-        const Words3 p = observer_words<A, TA, HI>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, seenf);
+        const Words3 p = observer_words<A, TA, HI, W2>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
         const int w = 3 * (a - T.ai0);
         uint64_t* o = T.ob + w;
         if (!T.emits) {
             ++a;
         } else if (T.v16 && !(w & 1) && a + 1 < end) {
-            const Words3 q = observer_words<A, TA, HI>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4,
-                                                   seenf);
+            const Words3 q = observer_words<A, TA, HI, W2>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4,
+                                                       P8, seenf);
             st16(o, p.o0, p.al);
             st16(o + 2, p.op, q.o0);
             st16(o + 4, q.al, q.op);
@@ -528,7 +582,7 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
     }
 }
 
-template <int A>
+template <int A, bool W2>
 __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const CtaShared& H, const EmitCtx& C,
                                                   uint32_t k, uint32_t e) {
     constexpr int NS = (A + 1) / 2, NW = (A + 3) / 4;
@@ -554,6 +608,14 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
         Ps[j] |= ((y * Ds + x) & 0xffu) << s8;
         Ph[j] |= ((y * Dh + x) & 0xffu) << s8;
     }
+    uint32_t Ps8[NW], Ph8[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        Ps8[j] = Ps[j] & 0x80808080u;
+        Ps[j] &= 0x7f7f7f7fu;
+        Ph8[j] = Ph[j] & 0x80808080u;
+        Ph[j] &= 0x7f7f7f7fu;
+    }
     uint32_t sl = C.base_slot + k;
     if (sl >= P.ring) sl -= P.ring;
     const bool emit_s = team_emits(E, 0), emit_h = team_emits(E, 1);
@@ -572,18 +634,22 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
     T.tbl = C.tbl + L.tbl_off[e][0];
     T.ai0 = 0;
     T.emits = emit_s;
-    if (Ds * Ds > 32u)
-        emit_team_fast<A, false, true>(T, rs, X4, Y4, Ps, seenf);
+    if (W2)
+        emit_team_fast<A, false, true, true>(T, rs, X4, Y4, Ps, Ps8, seenf);
+    else if (Ds * Ds > 32u)
+        emit_team_fast<A, false, true, false>(T, rs, X4, Y4, Ps, Ps8, seenf);
     else
-        emit_team_fast<A, false, false>(T, rs, X4, Y4, Ps, seenf);
+        emit_team_fast<A, false, false, false>(T, rs, X4, Y4, Ps, Ps8, seenf);
     if (A > 1 && emit_h) {
         T.tbl = C.tbl + L.tbl_off[e][1];
         T.ai0 = emit_s ? 0 : NS;
         T.emits = true;
-        if (Dh * Dh > 32u)
-            emit_team_fast<A, true, true>(T, rh, X4, Y4, Ph, seenf);
+        if (W2)
+            emit_team_fast<A, true, true, true>(T, rh, X4, Y4, Ph, Ph8, seenf);
+        else if (Dh * Dh > 32u)
+            emit_team_fast<A, true, true, false>(T, rh, X4, Y4, Ph, Ph8, seenf);
         else
-            emit_team_fast<A, true, false>(T, rh, X4, Y4, Ph, seenf);
+            emit_team_fast<A, true, false, false>(T, rh, X4, Y4, Ph, Ph8, seenf);
     }
     uint32_t seen = 0;
     if (done) {
@@ -616,14 +682,14 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
     }
 }
 
-template <int A>
+template <int A, bool W2>
 __device__ __forceinline__ void emit_segments_fast(const StepParams& P, const CtaShared& H, const EmitCtx& C) {
     const uint32_t ne = H.plan.n_envs;
     const uint32_t total = C.len * ne;
     const uint32_t dk = (uint32_t)C.n_workers / ne, de = (uint32_t)C.n_workers % ne;
     uint32_t k = (uint32_t)C.worker / ne, e = (uint32_t)C.worker % ne;
     for (uint32_t it = (uint32_t)C.worker; it < total; it += (uint32_t)C.n_workers) {
-        emit_segment_fast<A>(P, H, C, k, e);
+        emit_segment_fast<A, W2>(P, H, C, k, e);
         e += de;
         k += dk;
         if (e >= ne) {
@@ -637,11 +703,12 @@ __device__ __forceinline__ void emit_segments_fast(const StepParams& P, const Ct
 template <int FAM>
 __device__ __forceinline__ void emit_fast_dispatch(int A, const StepParams& P, const CtaShared& H,
                                                    const EmitCtx& C) {
-    constexpr int a0 = 4 * FAM - 3;
-    if (A == a0) emit_segments_fast<a0>(P, H, C);
-    else if (A == a0 + 1) emit_segments_fast<a0 + 1>(P, H, C);
-    else if (A == a0 + 2) emit_segments_fast<a0 + 2>(P, H, C);
-    else emit_segments_fast<a0 + 3>(P, H, C);
+    constexpr int a0 = 4 * ((FAM - 1) % 4) + 1;
+    constexpr bool W2 = FAM > 4;
+    if (A == a0) emit_segments_fast<a0, W2>(P, H, C);
+    else if (A == a0 + 1) emit_segments_fast<a0 + 1, W2>(P, H, C);
+    else if (A == a0 + 2) emit_segments_fast<a0 + 2, W2>(P, H, C);
+    else emit_segments_fast<a0 + 3, W2>(P, H, C);
 }
 
 // Per-cell shared state of the dynamics: a claim word (byte a-1 holds the
