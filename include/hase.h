@@ -81,6 +81,11 @@ typedef enum hase_status {
 #define HASE_ASYNC_CREATE 4u    /* hase_create does not wait for the world   */
                                 /* generation; a failed start-cell draw is   */
                                 /* reported by hase_sync and hase_digest     */
+#define HASE_DESYNC_START 16u  /* desynchronised start [Sec. 3.3, last    */
+                                /* paragraph]: env e's episode clock starts  */
+                                /* at floor(u * cap / 2^32), u = word 0 of   */
+                                /* Philox counter (0, 0, env, 3), at create  */
+                                /* and at every hase_reset                   */
 #define HASE_POOL_ALLOC 8u      /* buffers from the device's stream-ordered  */
                                 /* pool (allocated on the create stream,     */
                                 /* returned by hase_destroy on the stream of */

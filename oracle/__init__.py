@@ -65,6 +65,7 @@ def load_library(path):
     L.ho_destroy.argtypes = [P]
     L.ho_error.restype = C.c_char_p
     L.ho_reset.argtypes = [P]
+    L.ho_set_desync.argtypes = [P, C.c_int]
     L.ho_sizes.argtypes = [P, P, P, P]
     L.ho_offsets.argtypes = [P, P, P, P, P]
     L.ho_observe.argtypes = [P, P, P]
@@ -147,7 +148,7 @@ def observe_agent(S, grid, n_seekers, x, y, a, r, W=None, L=None):
 class World:
     """A batch of environments stepped by the oracle, outputs as numpy."""
 
-    def __init__(self, n_envs, seed, descs, env_id_base=0, L=None):
+    def __init__(self, n_envs, seed, descs, env_id_base=0, L=None, desync=False):
         self._L = L or lib()
         self._descs = env_array(descs)
         h = self._L.ho_create(n_envs, env_id_base, seed, C.cast(self._descs, C.c_void_p),
@@ -169,6 +170,8 @@ class World:
         self.words_per_plane = np.zeros(max(n_envs, 1), np.uint32)
         self._L.ho_offsets(self._h, _p(self.agent_off), _p(self.obs_off), _p(self.unp_off),
                            _p(self.words_per_plane))
+        if desync:
+            self._L.ho_set_desync(self._h, 1)
 
     def close(self):
         if getattr(self, "_h", None):

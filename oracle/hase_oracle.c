@@ -45,6 +45,7 @@ struct ho_world {
     int32_t *x, *y;         /* current positions, per agent            */
     uint32_t *ep_t;         /* steps into the current episode, per env */
     uint32_t *ep_idx;       /* finished episodes, per env              */
+    int desync;             /* episode clocks start at a drawn offset  */
 };
 
 static char g_err[256];
@@ -373,10 +374,30 @@ void ho_destroy(ho_world *w) {
     free(w);
 }
 
+/* Desynchronised start (Section 3.3, last paragraph: the envs of a batch are
+ * stepped stochastically at initialisation so that they do not all end their
+ * episodes together).  Reading: only the episode clock is offset -- env e
+ * starts its first episode at step floor(u * cap / 2^32), u = word 0 of the
+ * Philox block of counter (0, 0, env id, 3) -- so its first episode is that
+ * much shorter; positions start at the pristine cells and the action counter
+ * is untouched. */
+static uint32_t start_offset(const ho_world *w, uint32_t e) {
+    const uint32_t ctr[4] = {0u, 0u, w->env_id_base + e, 3u};
+    const uint32_t key[2] = {(uint32_t)(w->seed & 0xffffffffu), (uint32_t)(w->seed >> 32)};
+    uint32_t out[4];
+    ho_philox4x32_10(ctr, key, out);
+    return mulhi32(out[0], w->env[e].cap);
+}
+
+void ho_set_desync(ho_world *w, int on) {
+    w->desync = on ? 1 : 0;
+    ho_reset(w);
+}
+
 void ho_reset(ho_world *w) {
     w->t = 0;
     for (uint32_t e = 0; e < w->n_envs; ++e) {
-        w->ep_t[e] = 0;
+        w->ep_t[e] = w->desync ? start_offset(w, e) : 0;
         w->ep_idx[e] = 0;
         for (uint64_t i = w->agent_off[e]; i < w->agent_off[e + 1]; ++i) {
             w->x[i] = w->sx[i];

@@ -84,8 +84,14 @@ ho_world *ho_create(uint32_t n_envs, uint32_t env_id_base, uint64_t seed,
 void ho_destroy(ho_world *w);
 const char *ho_error(void);
 
-/* Back to t = 0 and the pristine state (start cells, ep_t = 0, episode 0). */
+/* Back to t = 0 and the pristine state (start cells, ep_t = 0, episode 0;
+ * with the desynchronised start, ep_t = the env's drawn offset). */
 void ho_reset(ho_world *w);
+
+/* Desynchronised start on (1) or off (0), then ho_reset.  With it on, env e's
+ * episode clock starts at floor(u * cap / 2^32), u = word 0 of the Philox
+ * block of counter (0, 0, env id, 3) (Section 3.3, last paragraph). */
+void ho_set_desync(ho_world *w, int on);
 
 /* Per-step output sizes: agents (rewards/actions), packed obs words and
  * unpacked obs bytes of one step over all envs. */

@@ -51,6 +51,7 @@ struct hase_handle {
         uint32_t first, count, smem, n_dyn, emit_warps, threads;
     };
     std::vector<Family> fams;
+    std::vector<EnvState> est0;  // episode clocks at create / reset
     uint64_t t = 0;
     uint64_t* d_clock = nullptr;  // steps enqueued before the running launch
     uint64_t* d_scratch = nullptr;  // digest partial sums [kDigestBlocks][3]
@@ -243,7 +244,8 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if (cfg->ring_steps < 1) return fail(nullptr, HASE_EINVAL, "ring_steps must be >= 1");
     if ((uint64_t)cfg->env_id_base + cfg->n_envs > 0x100000000ull)
         return fail(nullptr, HASE_EINVAL, "env ids exceed 32 bits");
-    if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED | HASE_ASYNC_CREATE | HASE_POOL_ALLOC))
+    if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED | HASE_ASYNC_CREATE | HASE_POOL_ALLOC |
+                       HASE_DESYNC_START))
         return fail(nullptr, HASE_EINVAL, "unknown flags 0x%x", cfg->flags);
     if (cfg->chunk_steps != 0 && (cfg->chunk_steps < 1 || cfg->chunk_steps > (uint32_t)kMaxChunk))
         return fail(nullptr, HASE_EINVAL, "chunk_steps outside 1..%d", kMaxChunk);
@@ -401,7 +403,18 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
                     "copy env list")) != HASE_OK) return s;
     if ((s = finish(cudaMemcpyAsync(h->d_groups, h->groups.data(), sizeof(Group) * h->groups.size(),
                                     cudaMemcpyHostToDevice, st), "copy groups")) != HASE_OK) return s;
-    if ((s = finish(cudaMemsetAsync(h->d_est, 0, sizeof(EnvState) * h->n_envs, st), "memset")) != HASE_OK)
+    // episode clocks: 0, or the desynchronised start offsets
+    h->est0.assign(h->n_envs, EnvState{0u, 0u});
+    if (h->flags & HASE_DESYNC_START) {
+        const uint32_t k0 = (uint32_t)(h->seed & 0xffffffffu), k1 = (uint32_t)(h->seed >> 32);
+        for (uint32_t e = 0; e < h->n_envs; ++e) {
+            uint32_t c0 = 0u, c1 = 0u, c2 = h->env[e].env_id, c3 = 3u;
+            philox4x32_10(c0, c1, c2, c3, k0, k1);
+            h->est0[e].ep_t = (uint32_t)(((uint64_t)c0 * h->env[e].cap) >> 32);
+        }
+    }
+    if ((s = finish(cudaMemcpyAsync(h->d_est, h->est0.data(), sizeof(EnvState) * h->n_envs,
+                                    cudaMemcpyHostToDevice, st), "copy clocks")) != HASE_OK)
         return s;
     if ((s = finish(cudaMemsetAsync(h->d_err, 0, 4, st), "memset")) != HASE_OK) return s;
     if ((s = finish(cudaMemsetAsync(h->d_clock, 0, 8, st), "memset")) != HASE_OK) return s;
@@ -445,7 +458,8 @@ hase_status hase_reset(hase_handle* h, void* stream) {
     h->last_stream = st;
     const uint64_t last = h->ring - 1;
     HASE_CUDA(h, cudaMemcpyAsync(h->d_pos, h->d_start, 2 * h->agents, cudaMemcpyDeviceToDevice, st));
-    HASE_CUDA(h, cudaMemsetAsync(h->d_est, 0, sizeof(EnvState) * h->n_envs, st));
+    HASE_CUDA(h, cudaMemcpyAsync(h->d_est, h->est0.data(), sizeof(EnvState) * h->n_envs, cudaMemcpyHostToDevice,
+                                 st));
     HASE_CUDA(h, cudaMemsetAsync(h->d_rew + last * h->agents, 0, 4 * h->agents, st));
     HASE_CUDA(h, cudaMemsetAsync(h->d_done + last * h->n_envs, 0, h->n_envs, st));
     if (h->d_act) HASE_CUDA(h, cudaMemsetAsync(h->d_act + last * h->agents, 0, h->agents, st));

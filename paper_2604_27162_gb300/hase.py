@@ -24,6 +24,7 @@ HASE_EXPORT_ACTIONS = 1
 HASE_EXPORT_UNPACKED = 2
 HASE_ASYNC_CREATE = 4
 HASE_POOL_ALLOC = 8
+HASE_DESYNC_START = 16
 HASE_OBS_SEEKERS = 1
 HASE_OBS_HIDERS = 2
 STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA",

@@ -42,7 +42,8 @@ def compare_run(n_envs, seed, descs, n_steps, ring=None, flags=hase.HASE_EXPORT_
     assert total == n_steps
     got = engine_outputs(eng)
     unpacked = bool(flags & hase.HASE_EXPORT_UNPACKED)
-    w = oracle.World(n_envs, seed, descs, env_id_base=env_id_base)
+    w = oracle.World(n_envs, seed, descs, env_id_base=env_id_base,
+                     desync=bool(flags & hase.HASE_DESYNC_START))
     if ring > n_steps:
         init = w.observe(unpacked=unpacked)
         o0 = init[0] if unpacked else init

@@ -84,6 +84,25 @@ def test_shared_memory_cap_too_small_rejected():
         hase.Engine(2, 1, [W.env_desc(64, 16, 8, 4, 4, 10, "0.2")], 8, smem_cap=16384)
 
 
+def test_desynchronised_start_matches_oracle():
+    c = W.ten1k()
+    descs = [dict(c["descs"][0], cap=29)]
+    flags = hase.HASE_EXPORT_ACTIONS | hase.HASE_DESYNC_START
+    compare_run(40, c["seed"], descs, 75, flags=flags)
+    compare_run(30, 4, W.uneven_descs(30, 8), 60, flags=flags, launches=[7, 53])
+    # a reset restores the same drawn offsets
+    eng = hase.Engine(25, 9, descs, 64, flags)
+    eng.step(40)
+    eng.reset()
+    eng.step(40)
+    got = engine_outputs(eng)
+    w = oracle.World(25, 9, descs, desync=True)
+    for t in range(40):
+        o = w.step()
+        assert (got["done"][t] == o["done"]).all() and (got["obs"][t] == o["obs"]).all(), t
+    eng.close()
+
+
 def test_ring_wraparound_and_split_launches():
     c = W.ten1k()
     compare_run(64, c["seed"], c["descs"], 300, ring=7, launches=[1, 2, 97, 200])

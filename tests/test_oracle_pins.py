@@ -459,3 +459,33 @@ def test_invalid_params_rejected():
         oracle.World(2, 0, [W.env_desc(4, 2, 3, 1, 1, 5, 0)])
     with pytest.raises(ValueError):
         oracle.World(2, 0, [W.env_desc(4, 2, 1, 1, 1, 0, 0)])
+
+
+def test_desynchronised_start():
+    """Section 3.3 (last paragraph): with the desynchronised start the first
+    episode of env e lasts cap - offset(e) steps, offsets spread uniformly over
+    [0, cap), positions start at the pristine cells, and every later episode
+    lasts cap steps."""
+    cap = 16
+    n = 4000
+    descs = [W.env_desc(8, 3, 2, 1, 1, cap, "0.1")]
+    plain = oracle.World(n, 21, descs)
+    w = oracle.World(n, 21, descs, desync=True)
+    s0, s1 = plain.state(), w.state()
+    x0, y0, ep0 = s0["x"], s0["y"], s0["ep_t"].astype(np.int64)
+    x1, y1, ep1 = s1["x"], s1["y"], s1["ep_t"].astype(np.int64)
+    assert np.array_equal(x0, x1) and np.array_equal(y0, y1)
+    assert (ep0 == 0).all() and ep1.min() >= 0 and ep1.max() < cap
+    counts = np.bincount(ep1, minlength=cap)
+    expected = n / cap
+    chi2 = float(((counts - expected) ** 2 / expected).sum())
+    assert chi2 < 40.0, chi2  # 15 degrees of freedom, p ~ 5e-4
+    first = np.full(n, -1)
+    ends = [[] for _ in range(n)]
+    for t in range(3 * cap):
+        d = w.step()["done"]
+        for e in np.flatnonzero(d):
+            ends[e].append(t)
+    for e in range(n):
+        assert ends[e][0] == cap - 1 - ep1[e], e
+        assert all(b - a == cap for a, b in zip(ends[e], ends[e][1:])), e
