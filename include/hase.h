@@ -94,6 +94,12 @@ typedef enum hase_status {
 /* Observation emitters (hase_env_desc.obs_teams). */
 #define HASE_OBS_SEEKERS 1u
 #define HASE_OBS_HIDERS 2u
+#define HASE_OBS_LOS 4u     /* line of sight [Sec. 3.1]: a window cell is seen   */
+                            /* iff every cell strictly between it and the agent  */
+                            /* on the discrete line (rnd(i dx/n), rnd(i dy/n)),  */
+                            /* i = 1..n-1, n = max(|dx|,|dy|), rnd rounding      */
+                            /* halves away from zero, is in the grid and free;   */
+                            /* unseen cells read 0 in all three planes           */
 
 /* One environment's parameters.  Seekers are agents 0..n_seekers-1, hiders
  * n_seekers..n_agents-1.  obs_teams = 0 writes no observation (the paper's

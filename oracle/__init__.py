@@ -59,7 +59,9 @@ def load_library(path):
     L.ho_action.restype = u32
     L.ho_move.argtypes = [u32, P, u32, P, P, P, P, P]
     L.ho_reward.argtypes = [u32, u32, u32, P, P, P]
-    L.ho_observe_agent.argtypes = [u32, P, u32, u32, P, P, u32, u32, u32, P]
+    L.ho_observe_agent.argtypes = [u32, P, u32, u32, P, P, u32, u32, u32, u32, P]
+    L.ho_visible.argtypes = [u32, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    L.ho_visible.restype = C.c_int
     L.ho_create.argtypes = [u32, u32, u64, P, u32]
     L.ho_create.restype = P
     L.ho_destroy.argtypes = [P]
@@ -134,14 +136,19 @@ def reward(n_seekers, r_seek, x, y, L=None):
     return rew
 
 
-def observe_agent(S, grid, n_seekers, x, y, a, r, W=None, L=None):
+def visible(S, grid, x, y, dx, dy, L=None):
+    grid = np.ascontiguousarray(grid, dtype=np.uint8)
+    return bool((L or lib()).ho_visible(S, _p(grid), x, y, dx, dy))
+
+
+def observe_agent(S, grid, n_seekers, x, y, a, r, W=None, L=None, los=False):
     if W is None:
         W = ((2 * r + 1) ** 2 + 63) // 64
     grid = np.ascontiguousarray(grid, dtype=np.uint8)
     x = np.ascontiguousarray(x, dtype=np.int32)
     y = np.ascontiguousarray(y, dtype=np.int32)
     out = np.zeros(3 * W, dtype=np.uint64)
-    (L or lib()).ho_observe_agent(S, _p(grid), len(x), n_seekers, _p(x), _p(y), a, r, W, _p(out))
+    (L or lib()).ho_observe_agent(S, _p(grid), len(x), n_seekers, _p(x), _p(y), a, r, W, int(los), _p(out))
     return out.reshape(3, W)
 
 

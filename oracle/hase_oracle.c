@@ -178,9 +178,30 @@ void ho_reward(uint32_t A, uint32_t n_seekers, uint32_t r_seek, const int32_t *x
 /* the grid.  Plane 1: an agent of a's team other than a.  Plane 2: an agent */
 /* of the other team.                                                        */
 /* ------------------------------------------------------------------------ */
+/* Line of sight (Section 3.1: the observation is a line-of-sight projection
+ * of the true state).  Reading: window cell (dx, dy) is visible from the
+ * agent's cell iff every cell strictly between them on the discrete line is
+ * inside the grid and free of obstacles; with n = max(|dx|, |dy|) those cells
+ * are (rnd(i dx / n), rnd(i dy / n)) for i = 1 .. n-1, rnd rounding halves
+ * away from zero. */
+static int32_t rnd_div(int32_t p, int32_t n) {
+    return p >= 0 ? (2 * p + n) / (2 * n) : -((-2 * p + n) / (2 * n));
+}
+
+int ho_visible(uint32_t S, const uint8_t *grid, int32_t x, int32_t y, int32_t dx, int32_t dy) {
+    int32_t n = abs(dx) > abs(dy) ? abs(dx) : abs(dy);
+    for (int32_t i = 1; i < n; ++i) {
+        int32_t cx = x + rnd_div(i * dx, n);
+        int32_t cy = y + rnd_div(i * dy, n);
+        if (cx < 0 || cy < 0 || cx >= (int32_t)S || cy >= (int32_t)S) return 0;
+        if (grid[(size_t)cy * S + (size_t)cx]) return 0;
+    }
+    return 1;
+}
+
 void ho_observe_agent(uint32_t S, const uint8_t *grid, uint32_t A, uint32_t n_seekers,
                       const int32_t *x, const int32_t *y, uint32_t a, uint32_t r,
-                      uint32_t W, uint64_t *out) {
+                      uint32_t W, uint32_t los, uint64_t *out) {
     int32_t R = (int32_t)r;
     int32_t D = 2 * R + 1;
     int team_a = a < n_seekers ? 0 : 1;
@@ -192,6 +213,7 @@ void ho_observe_agent(uint32_t S, const uint8_t *grid, uint32_t A, uint32_t n_se
             uint32_t word = k / 64;
             int32_t cx = x[a] + dx;
             int32_t cy = y[a] + dy;
+            if (los && !ho_visible(S, grid, x[a], y[a], dx, dy)) continue;  /* hidden: all planes 0 */
             if (cx < 0 || cy < 0 || cx >= (int32_t)S || cy >= (int32_t)S) {
                 out[0 * W + word] |= bit;
                 continue;
@@ -308,6 +330,10 @@ static int check_env(const ho_env *p) {
     }
     if (p->cap < 1) {
         snprintf(g_err, sizeof g_err, "episode cap must be >= 1");
+        return 0;
+    }
+    if (p->obs_teams > 7) {
+        snprintf(g_err, sizeof g_err, "obs_teams %u: bits 0-2 only", p->obs_teams);
         return 0;
     }
     return 1;
@@ -435,7 +461,7 @@ static void observe_env(const ho_world *w, uint32_t e, uint64_t *obs, uint8_t *u
         if (!emits(p, a)) continue;
         uint32_t r = radius_of(p, a);
         ho_observe_agent(p->side, w->grid[e], p->n_agents, p->n_seekers, &w->x[base],
-                         &w->y[base], a, r, W, tmp);
+                         &w->y[base], a, r, W, (p->obs_teams >> 2) & 1u, tmp);
         if (obs) {
             for (uint32_t i = 0; i < 3 * W; ++i) obs[oi + i] = tmp[i];
         }

@@ -48,7 +48,8 @@ typedef struct ho_env {
     uint32_t r_hide;      /* hider view radius                                 */
     uint32_t cap;         /* episode length in steps (truncation)              */
     uint32_t density_thr; /* cell is an obstacle iff its Philox word < thr     */
-    uint32_t obs_teams;   /* bit0 seekers emit obs, bit1 hiders emit obs       */
+    uint32_t obs_teams;   /* bit0 seekers emit obs, bit1 hiders emit obs,      */
+                          /* bit2 line of sight masks the windows           */
 } ho_env;
 
 typedef struct ho_world ho_world;
@@ -74,7 +75,13 @@ void ho_reward(uint32_t A, uint32_t n_seekers, uint32_t r_seek, const int32_t *x
  * r is the agent's radius; W must be >= ceil((2r+1)^2 / 64). */
 void ho_observe_agent(uint32_t S, const uint8_t *grid, uint32_t A, uint32_t n_seekers,
                       const int32_t *x, const int32_t *y, uint32_t a, uint32_t r,
-                      uint32_t W, uint64_t *out);
+                      uint32_t W, uint32_t los, uint64_t *out);
+
+/* Line of sight (Section 3.1): window cell (dx, dy) of an agent at (x, y) is
+ * visible iff every cell strictly between them on the discrete line is inside
+ * the grid and free; the line's cells are (rnd(i dx / n), rnd(i dy / n)),
+ * i = 1 .. n-1, n = max(|dx|, |dy|), rnd rounding halves away from zero. */
+int ho_visible(uint32_t S, const uint8_t *grid, int32_t x, int32_t y, int32_t dx, int32_t dy);
 
 /* World of n_envs environments with global ids env_id_base + e.  envs holds
  * n_desc entries: 1 (broadcast to every env) or n_envs.  Returns NULL on an

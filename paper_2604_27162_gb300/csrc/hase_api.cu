@@ -140,7 +140,7 @@ static hase_status validate(const hase_env_desc& d, uint32_t i) {
         return fail(nullptr, HASE_EINVAL, "env desc %u: view radius above %d", i, HASE_MAX_RADIUS);
     if (d.cap < 1 || d.cap > 0x7fffffffu)
         return fail(nullptr, HASE_EINVAL, "env desc %u: episode cap outside 1..2^31-1", i);
-    if (d.obs_teams > 3u) return fail(nullptr, HASE_EINVAL, "env desc %u: obs_teams must be 0..3", i);
+    if (d.obs_teams > 7u) return fail(nullptr, HASE_EINVAL, "env desc %u: obs_teams must be 0..7", i);
     return HASE_OK;
 }
 

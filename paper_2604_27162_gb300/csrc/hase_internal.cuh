@@ -27,6 +27,7 @@ constexpr int kMaxGroupSlots = 128;   // agents per CTA (four dynamics warps)
 constexpr int kMaxDyn = 4;            // dynamics warps per CTA
 constexpr int kMaxChunk = 64;         // steps per on-chip chunk
 constexpr int kObsHiders = 2;         // obs_teams value: only hiders emit
+constexpr uint32_t kObsLos = 4;       // obs_teams bit: line of sight masks the windows
 constexpr uint32_t kDoneBit = 0x8000u;
 constexpr uint32_t kOccBit = 0x80u;   // occupancy bit of the neighbour map
 constexpr uint32_t kSmemBudget = 216 * 1024;  // dynamic shared memory per CTA
@@ -69,9 +70,16 @@ struct Group {
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 __host__ __device__ inline bool team_emits(const EnvRT& E, int team) { return (E.obs_teams >> team) & 1u; }
+__host__ __device__ inline bool only_hiders_emit(const EnvRT& E) { return (E.obs_teams & 3u) == (uint32_t)kObsHiders; }
+__host__ __device__ inline bool line_of_sight(const EnvRT& E) { return (E.obs_teams & kObsLos) != 0u; }
 __host__ __device__ inline int team_radius(const EnvRT& E, int team) { return team ? E.r_hide : E.r_seek; }
 __host__ __device__ inline uint32_t words_of_radius(int r) {
     return (uint32_t)(((2 * r + 1) * (2 * r + 1) + 63) / 64);
+}
+// uint64 words of one window-table entry: the obstacle plane, then (with
+// line of sight) the visibility mask
+__host__ __device__ inline uint32_t table_words(const EnvRT& E, int r) {
+    return words_of_radius(r) * (line_of_sight(E) ? 2u : 1u);
 }
 
 // Inside a CTA a cell is packed as x | y << sh with sh = 5 for grids up to
@@ -95,9 +103,10 @@ struct GroupPlan {
 };
 
 // One thread emits a whole (step, env) when the seekers are the first
-// ceil(A / 2) agents (windows of up to two words a plane).
+// ceil(A / 2) agents (windows of up to two words a plane) and no line of
+// sight masks the windows; other shapes take the lane-per-agent emission.
 __host__ __device__ inline bool fast_emission(const EnvRT& E) {
-    return E.wpp <= 2 && E.n_seekers == (E.n_agents + 1u) / 2u;
+    return E.wpp <= 2 && E.n_seekers == (E.n_agents + 1u) / 2u && !(E.obs_teams & kObsLos);
 }
 
 // Kernel families: family 0 runs the general (lane per agent) emission;
@@ -141,7 +150,7 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
                 continue;
             }
             G.tbl_off[i][t] = to;
-            to += (uint32_t)E.side * E.side * words_of_radius(team_radius(E, t));
+            to += (uint32_t)E.side * E.side * table_words(E, team_radius(E, t));
         }
     }
     G.n_dyn = (uint32_t)dyn + 1;

@@ -107,7 +107,15 @@ __global__ void observe_kernel(const EnvRT* __restrict__ env, uint32_t n_envs,
     obstacle_plane(rows + E.rows_off, E.rw, px(p), py(p), r, pl[0][0], pl[0][1]);
     team_planes_pairwise(px(p), py(p), r, a, E.n_agents, ns, pos + E.agent_off, pl[1][0], pl[1][1],
                          pl[2][0], pl[2][1]);
-    const int ai = (E.obs_teams == kObsHiders) ? a - ns : a;
+    if (line_of_sight(E)) {  // hidden cells read 0 in every plane
+        uint64_t vl, vh;
+        window_visibility(pl[0][0], pl[0][1], r, vl, vh);
+        for (int q = 0; q < 3; ++q) {
+            pl[q][0] &= vl;
+            pl[q][1] &= vh;
+        }
+    }
+    const int ai = only_hiders_emit(E) ? a - ns : a;
     const int W = E.wpp;
     uint64_t* o = obs + E.obs_off + (uint64_t)ai * 3 * W;
     for (int q = 0; q < 3; ++q)

@@ -80,6 +80,31 @@ __device__ __forceinline__ void obstacle_plane(const uint64_t* rows, int rw, int
     for (int dy = 0; dy < D; ++dy) or_bits(lo, hi, row_bits(row + dy * rw, rw, s, mask), dy * D);
 }
 
+// Line of sight: window cell (dx, dy) is visible iff every cell strictly
+// between it and the centre on the discrete line -- (rnd(i dx / n),
+// rnd(i dy / n)) for i = 1 .. n-1, n = max(|dx|, |dy|), rnd rounding halves
+// away from zero -- is free in the window's obstacle plane (lo, hi), whose
+// out-of-grid cells are already set.
+__host__ __device__ inline int rnd_half_away(int p, int n) {
+    return p >= 0 ? (2 * p + n) / (2 * n) : -((-2 * p + n) / (2 * n));
+}
+
+__device__ inline void window_visibility(uint64_t lo, uint64_t hi, int r, uint64_t& vlo, uint64_t& vhi) {
+    const int D = 2 * r + 1;
+    vlo = vhi = 0;
+    for (int dy = -r; dy <= r; ++dy) {
+        for (int dx = -r; dx <= r; ++dx) {
+            const int n = max(abs(dx), abs(dy));
+            bool vis = true;
+            for (int i = 1; i < n && vis; ++i) {
+                const int k = (rnd_half_away(i * dy, n) + r) * D + (rnd_half_away(i * dx, n) + r);
+                vis = !(((k < 64 ? lo : hi) >> (k & 63)) & 1ull);
+            }
+            if (vis) set_bit(vlo, vhi, (dy + r) * D + (dx + r));
+        }
+    }
+}
+
 // Ally / opponent planes of agent a from the packed positions P[0..A)
 // (pairwise; used for small groups and by the step -1 observation).
 __device__ __forceinline__ void team_planes_pairwise(int x, int y, int r, int a, int A, int ns,
@@ -192,7 +217,7 @@ __device__ __forceinline__ void emit_chunk(const StepParams& P, const CtaShared&
     const uint32_t twoR = (uint32_t)(2 * R);
     const int rs = E0.r_seek;
     const bool emits = team_emits(E0, ta ? 1 : 0);
-    const int ai = (E0.obs_teams == kObsHiders) ? a - ns : a;
+    const int ai = only_hiders_emit(E0) ? a - ns : a;
     const int W64 = E0.wpp;
     const bool use_table = L.flags & kUseTable;
     const uint32_t n_items = C.len * ne;
@@ -277,21 +302,43 @@ __device__ __forceinline__ void emit_chunk(const StepParams& P, const CtaShared&
             if (P.act_out)
                 P.act_out[(uint64_t)sl * P.agents + E.agent_off + a] = C.act[act_index(kk, (uint32_t)(first + a), nsl)];
             if (emits) {
-                // a5 obstacle plane
-                Plane<NW> o0;
+                // a5 obstacle plane (and, with line of sight, the visible cells)
+                Plane<NW> o0, vis;
+                vis.lo = ~0ull;
+                vis.hi = ~0u;
+                const bool los = line_of_sight(E);
                 if (use_table) {
                     const uint32_t W = words_of_radius(R);
-                    const uint64_t* tw = C.tbl + L.tbl_off[ee][ta ? 1 : 0] + (uint32_t)(yo * E.side + xo) * W;
+                    const uint64_t* tw =
+                        C.tbl + L.tbl_off[ee][ta ? 1 : 0] + (uint32_t)(yo * E.side + xo) * table_words(E, R);
                     o0.lo = tw[0];
                     o0.hi = (NW == 3 && W == 2) ? (uint32_t)tw[1] : 0u;
+                    if (los) {
+                        vis.lo = tw[W];
+                        vis.hi = (NW == 3 && W == 2) ? (uint32_t)tw[W + 1] : 0u;
+                    }
                 } else {
                     uint64_t lo, hi;
                     obstacle_plane(C.rows + L.rows_off[ee], E.rw, xo, yo, R, lo, hi);
                     o0.lo = lo;
                     o0.hi = (uint32_t)hi;
+                    if (los) {
+                        uint64_t vl, vh;
+                        window_visibility(lo, hi, R, vl, vh);
+                        vis.lo = vl;
+                        vis.hi = (uint32_t)vh;
+                    }
                 }
-                const Plane<NW>& al = ta ? ph : ps;
-                const Plane<NW>& opp = ta ? ps : ph;
+                Plane<NW> al = ta ? ph : ps;
+                Plane<NW> opp = ta ? ps : ph;
+                if (los) {  // hidden cells read 0 in every plane
+                    o0.lo &= vis.lo;
+                    o0.hi &= vis.hi;
+                    al.lo &= vis.lo;
+                    al.hi &= vis.hi;
+                    opp.lo &= vis.lo;
+                    opp.hi &= vis.hi;
+                }
                 uint64_t* o = P.obs + (uint64_t)sl * P.obs_words + E.obs_off + (uint32_t)ai * 3u * (uint32_t)W64;
                 if (W64 == 1) {
                     o[0] = o0.lo;
@@ -805,13 +852,20 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                 if (L.tbl_off[i][t] == ~0u) continue;
                 if (t == 1 && L.tbl_off[i][1] == L.tbl_off[i][0]) continue;
                 const int r = team_radius(E, t);
-                const uint32_t W = words_of_radius(r);
+                const uint32_t W = words_of_radius(r), Wt = table_words(E, r);
+                const bool los = line_of_sight(E);
                 uint64_t* Tb = s_tbl + L.tbl_off[i][t];
                 for (int c = tid; c < S * S; c += nthreads) {
                     uint64_t lo, hi;
                     obstacle_plane(Rw, rw, c % S, c / S, r, lo, hi);
-                    Tb[c * W] = lo;
-                    if (W == 2) Tb[c * W + 1] = hi;
+                    Tb[c * Wt] = lo;
+                    if (W == 2) Tb[c * Wt + 1] = hi;
+                    if (los) {  // then the visible cells of the window
+                        uint64_t vl, vh;
+                        window_visibility(lo, hi, r, vl, vh);
+                        Tb[c * Wt + W] = vl;
+                        if (W == 2) Tb[c * Wt + W + 1] = vh;
+                    }
                 }
             }
         }

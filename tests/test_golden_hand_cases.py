@@ -41,7 +41,8 @@ def _grid(c):
 
 def test_hand_cases_cover_every_rule():
     names = [c["name"] for c in _cases()]
-    assert {"obs_inside", "obs_corner", "obs_radius4_two_words", "moves", "rewards"} <= set(names)
+    assert {"obs_inside", "obs_corner", "obs_radius4_two_words", "obs_line_of_sight", "moves",
+            "rewards"} <= set(names)
     assert all("cite" in c for c in _cases())
 
 
@@ -53,7 +54,8 @@ def test_observation_windows():
         x, y = _xy(c["agents"])
         r = int(c["radius"])
         W = ((2 * r + 1) ** 2 + 63) // 64
-        got = oracle.observe_agent(S, grid, int(c["seekers"]), x, y, int(c["observer"]), r, W)
+        got = oracle.observe_agent(S, grid, int(c["seekers"]), x, y, int(c["observer"]), r, W,
+                                   los=bool(int(c.get("los", "0"))))
         for p in range(3):
             want = [int(v) for v in c["plane%d" % p].split()]
             want += [0] * (W - len(want))
@@ -75,3 +77,25 @@ def test_rewards():
     x, y = _xy(c["agents"])
     got = oracle.reward(int(c["seekers"]), int(c["radius"]), x, y)
     assert list(got) == [int(v) for v in c["expect"].split()]
+
+
+def test_line_of_sight_properties():
+    """Without obstacles every window cell is visible; a full wall one row
+    below the agent hides every cell two or more rows below it and leaves the
+    cells straight below and diagonally adjacent visible."""
+    S, r = 11, 4
+    empty = np.zeros(S * S, np.uint8)
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            assert oracle.visible(S, empty, 5, 5, dx, dy)
+    wall = np.zeros((S, S), np.uint8)
+    wall[6, :] = 1
+    wall = wall.reshape(-1)
+    for dy in range(2, r + 1):
+        for dx in range(-r, r + 1):
+            assert not oracle.visible(S, wall, 5, 5, dx, dy), (dx, dy)
+    for dx in (-1, 0, 1):
+        assert oracle.visible(S, wall, 5, 5, dx, 1)
+    # cells outside the grid block the view beyond them
+    assert not oracle.visible(S, empty, 0, 5, -2, 0)
+    assert oracle.visible(S, empty, 0, 5, -1, 0)

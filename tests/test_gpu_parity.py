@@ -103,6 +103,22 @@ def test_desynchronised_start_matches_oracle():
     eng.close()
 
 
+@pytest.mark.parametrize("desc", [
+    W.env_desc(32, 10, 5, 3, 2, 40, "0.2", 3 | 4),     # one-thread emission, radius 3 / 2
+    W.env_desc(24, 7, 4, 4, 4, 40, "0.25", 3 | 4),     # one-thread emission, radius 4 (two words)
+    W.env_desc(16, 6, 2, 3, 1, 30, "0.3", 3 | 4),      # lane-per-agent emission
+    W.env_desc(12, 5, 3, 2, 2, 30, "0.2", 2 | 4),      # hiders only emit
+])
+def test_line_of_sight_matches_oracle(desc):
+    compare_run(36, 17, [desc], 70, flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED)
+    compare_run(20, 18, [desc], 40, smem_cap=32768)  # windows computed without tables
+
+
+def test_line_of_sight_uneven():
+    descs = [dict(d, obs_teams=3 | 4) for d in W.uneven_descs(40, 11)]
+    compare_run(40, 19, descs, 60)
+
+
 def test_ring_wraparound_and_split_launches():
     c = W.ten1k()
     compare_run(64, c["seed"], c["descs"], 300, ring=7, launches=[1, 2, 97, 200])
@@ -174,7 +190,7 @@ def test_invalid_configs_rejected():
     good = W.ten1k()["descs"][0]
     for bad in (dict(good, side=65), dict(good, side=1), dict(good, n_agents=17),
                 dict(good, n_agents=0), dict(good, n_seekers=11), dict(good, r_seek=5),
-                dict(good, cap=0), dict(good, obs_teams=4)):
+                dict(good, cap=0), dict(good, obs_teams=8)):
         with pytest.raises(hase.HaseError) as ei:
             hase.Engine(4, 0, [bad], 2)
         assert ei.value.status == hase.HASE_EINVAL
