@@ -40,6 +40,8 @@
  *   actions  uint8  [agents]     (only with HASE_EXPORT_ACTIONS)
  *   unpacked uint8  [unp_bytes]  env e at unp_off[e]: [A_obs][3][2r+1][2r+1]
  *                                (only with HASE_EXPORT_UNPACKED)
+ *   central  uint64 [central_words] env e at central_off[e]: [4][S]
+ *                                (only with HASE_EXPORT_CENTRAL)
  * A_obs(e) counts the agents whose team emits observations (seekers first).
  * Pointers returned by the *_ptr calls stay valid until hase_destroy; their
  * contents are valid once the stream work that wrote them has completed.
@@ -81,6 +83,13 @@ typedef enum hase_status {
 #define HASE_ASYNC_CREATE 4u    /* hase_create does not wait for the world   */
                                 /* generation; a failed start-cell draw is   */
                                 /* reported by hase_sync and hase_digest     */
+#define HASE_EXPORT_CENTRAL 32u /* also write the centralized observation   */
+                                /* [Sec. 3.3, mode 3]: per env four planes   */
+                                /* over its grid -- 0 cells inside some      */
+                                /* observing agent's window (visible to it   */
+                                /* with HASE_OBS_LOS), 1 seen obstacles,     */
+                                /* 2 seen seekers, 3 seen hiders -- each S   */
+                                /* rows of one uint64 (bit x = column x)     */
 #define HASE_DESYNC_START 16u  /* desynchronised start [Sec. 3.3, last    */
                                 /* paragraph]: env e's episode clock starts  */
                                 /* at floor(u * cap / 2^32), u = word 0 of   */
@@ -145,6 +154,8 @@ typedef struct hase_layout {
     const uint64_t *agent_off;
     const uint64_t *obs_off;
     const uint64_t *unp_off;
+    uint64_t central_words;  /* centralized observation words per slot     */
+    const uint64_t *central_off; /* env e at central_off[e]: [4][side] words */
 } hase_layout;
 
 typedef struct hase_handle hase_handle;
@@ -178,6 +189,7 @@ hase_status hase_obs_ptr(hase_handle *h, uint64_t **packed, uint8_t **unpacked);
 hase_status hase_reward_ptr(hase_handle *h, int32_t **reward);
 hase_status hase_done_ptr(hase_handle *h, uint8_t **done);
 hase_status hase_actions_ptr(hase_handle *h, uint8_t **actions);
+hase_status hase_central_ptr(hase_handle *h, uint64_t **central);
 hase_status hase_layout_get(hase_handle *h, hase_layout *out);
 
 /* The same n_steps as one CUDA graph: the first call for a given n_steps

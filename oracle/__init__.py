@@ -68,6 +68,10 @@ def load_library(path):
     L.ho_error.restype = C.c_char_p
     L.ho_reset.argtypes = [P]
     L.ho_set_desync.argtypes = [P, C.c_int]
+    L.ho_central_words.argtypes = [P]
+    L.ho_central_words.restype = u64
+    L.ho_central.argtypes = [P, P]
+    L.ho_central_one.argtypes = [u32, P, u32, u32, u32, u32, u32, P, P, P]
     L.ho_sizes.argtypes = [P, P, P, P]
     L.ho_offsets.argtypes = [P, P, P, P, P]
     L.ho_observe.argtypes = [P, P, P]
@@ -139,6 +143,18 @@ def reward(n_seekers, r_seek, x, y, L=None):
 def visible(S, grid, x, y, dx, dy, L=None):
     grid = np.ascontiguousarray(grid, dtype=np.uint8)
     return bool((L or lib()).ho_visible(S, _p(grid), x, y, dx, dy))
+
+
+def central_one(S, grid, n_seekers, r_seek, r_hide, obs_teams, x, y, L=None):
+    """Centralized observation of one env: array [4][S][ceil(S/64)]."""
+    grid = np.ascontiguousarray(grid, dtype=np.uint8)
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    rw = (S + 63) // 64
+    out = np.zeros(4 * S * rw, dtype=np.uint64)
+    (L or lib()).ho_central_one(S, _p(grid), len(x), n_seekers, r_seek, r_hide, obs_teams, _p(x), _p(y),
+                                _p(out))
+    return out.reshape(4, S, rw)
 
 
 def observe_agent(S, grid, n_seekers, x, y, a, r, W=None, L=None, los=False):
@@ -213,6 +229,12 @@ class World:
         if unpacked:
             out["unpacked"] = unp
         return out
+
+    def central(self):
+        """Centralized observation of the current state (all envs)."""
+        out = np.zeros(max(1, int(self._L.ho_central_words(self._h))), np.uint64)
+        self._L.ho_central(self._h, _p(out))
+        return out[: int(self._L.ho_central_words(self._h))]
 
     def state(self):
         n = self.n_agents_total

@@ -244,6 +244,65 @@ static uint32_t radius_of(const ho_env *p, uint32_t a) {
     return a < p->n_seekers ? p->r_seek : p->r_hide;
 }
 
+/* Centralized observation (Section 3.3, observability mode 3: all agents'
+ * sightlines fused into one shared partial observation).  Reading: one
+ * tensor per env over its whole grid with four planes -- 0 cells seen by
+ * some observing agent (inside its window; with line of sight, visible to
+ * it), 1 seen obstacles, 2 seen seekers, 3 seen hiders.  Plane p, row y,
+ * bit x of word x / 64 is cell (x, y); S rows of ceil(S / 64) words. */
+void ho_central_one(uint32_t side, const uint8_t *grid, uint32_t A, uint32_t n_seekers, uint32_t r_seek,
+                    uint32_t r_hide, uint32_t obs_teams, const int32_t *ax, const int32_t *ay, uint64_t *out) {
+    const int32_t S = (int32_t)side;
+    const uint32_t rw = (side + 63u) / 64u;
+    const uint32_t los = (obs_teams >> 2) & 1u;
+    for (uint64_t i = 0; i < 4ull * S * rw; ++i) out[i] = 0;
+    for (int32_t y = 0; y < S; ++y) {
+        for (int32_t x = 0; x < S; ++x) {
+            int seen = 0;
+            for (uint32_t a = 0; a < A && !seen; ++a) {
+                const uint32_t team = a < n_seekers ? 0u : 1u;
+                if (!((obs_teams >> team) & 1u)) continue;
+                const int32_t r = (int32_t)(team ? r_hide : r_seek);
+                const int32_t dx = x - ax[a], dy = y - ay[a];
+                if (dx < -r || dx > r || dy < -r || dy > r) continue;
+                if (los && !ho_visible(side, grid, ax[a], ay[a], dx, dy)) continue;
+                seen = 1;
+            }
+            if (!seen) continue;
+            const uint64_t bit = (uint64_t)1 << (x % 64);
+            const uint64_t at = (uint64_t)y * rw + (uint64_t)(x / 64);
+            out[0 * S * rw + at] |= bit;
+            if (grid[(size_t)y * S + (size_t)x]) out[1 * S * rw + at] |= bit;
+            for (uint32_t b = 0; b < A; ++b) {
+                if (ax[b] != x || ay[b] != y) continue;
+                out[(b < n_seekers ? 2 : 3) * S * rw + at] |= bit;
+            }
+        }
+    }
+}
+
+static void central_env(const ho_world *w, uint32_t e, uint64_t *out) {
+    const ho_env *p = &w->env[e];
+    const uint64_t base = w->agent_off[e];
+    ho_central_one(p->side, w->grid[e], p->n_agents, p->n_seekers, p->r_seek, p->r_hide, p->obs_teams,
+                   &w->x[base], &w->y[base], out);
+}
+
+uint64_t ho_central_words(const ho_world *w) {
+    uint64_t n = 0;
+    for (uint32_t e = 0; e < w->n_envs; ++e) n += 4ull * w->env[e].side * ((w->env[e].side + 63u) / 64u);
+    return n;
+}
+
+void ho_central(const ho_world *w, uint64_t *out) {
+    uint64_t off = 0;
+    for (uint32_t e = 0; e < w->n_envs; ++e) {
+        central_env(w, e, out + off);
+        off += 4ull * w->env[e].side * ((w->env[e].side + 63u) / 64u);
+    }
+}
+
+
 static uint32_t words_per_plane(const ho_env *p) {
     uint32_t wmax = 0;
     for (uint32_t a = 0; a < p->n_agents; ++a) {

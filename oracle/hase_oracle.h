@@ -95,6 +95,17 @@ const char *ho_error(void);
  * with the desynchronised start, ep_t = the env's drawn offset). */
 void ho_reset(ho_world *w);
 
+/* Centralized observation of the current state (Section 3.3, observability
+ * mode 3), every env in order: four planes (0 seen by some observing agent,
+ * 1 seen obstacles, 2 seen seekers, 3 seen hiders), each S rows of
+ * ceil(S / 64) words, bit x % 64 of word x / 64 of row y = cell (x, y).
+ * ho_central_words gives the words of all envs. */
+uint64_t ho_central_words(const ho_world *w);
+/* The same for one env given its grid and agent cells (out: 4 S ceil(S/64)). */
+void ho_central_one(uint32_t side, const uint8_t *grid, uint32_t A, uint32_t n_seekers, uint32_t r_seek,
+                    uint32_t r_hide, uint32_t obs_teams, const int32_t *x, const int32_t *y, uint64_t *out);
+void ho_central(const ho_world *w, uint64_t *out);
+
 /* Desynchronised start on (1) or off (0), then ho_reset.  With it on, env e's
  * episode clock starts at floor(u * cap / 2^32), u = word 0 of the Philox
  * block of counter (0, 0, env id, 3) (Section 3.3, last paragraph). */

@@ -23,6 +23,8 @@ cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* po
 cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
                         cudaStream_t st);
 cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st);
+cudaError_t launch_central_init(const EnvRT* env, uint32_t n_envs, const uint16_t* pos, const uint64_t* rows,
+                                const uint32_t* coff, uint64_t* central, cudaStream_t st);
 cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
                           uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
                           uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
@@ -41,7 +43,10 @@ struct hase_handle {
     std::vector<uint32_t> thr;
     std::vector<Group> groups;
     std::vector<uint32_t> env_list;
-    std::vector<uint64_t> agent_off, obs_off, unp_off;
+    std::vector<uint64_t> agent_off, obs_off, unp_off, central_off;
+    uint64_t central_words = 0;
+    uint64_t* d_central = nullptr;
+    uint32_t* d_coff = nullptr;
     uint64_t agents = 0, obs_words = 0, unp_bytes = 0, rows_words = 0;
     uint32_t smem = 0, threads = 0, kc = 16, emit_warps = 0, steps_per_launch = 0, n_dyn = 1;
     uint32_t smem_budget = kSmemBudget;
@@ -105,7 +110,7 @@ static hase_status cuda_fail(hase_handle* h, cudaError_t e, const char* what) {
 static void free_all(hase_handle* h) {
     void* ptrs[] = {h->d_env, h->d_est,  h->d_pos, h->d_start, h->d_rows, h->d_groups,
                     h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr, h->d_env_list,
-                    h->d_clock, h->d_scratch};
+                    h->d_clock, h->d_scratch, h->d_central, h->d_coff};
     const bool pool = h->flags & HASE_POOL_ALLOC;
     for (void* p : ptrs)
         if (p) {
@@ -245,7 +250,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if ((uint64_t)cfg->env_id_base + cfg->n_envs > 0x100000000ull)
         return fail(nullptr, HASE_EINVAL, "env ids exceed 32 bits");
     if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED | HASE_ASYNC_CREATE | HASE_POOL_ALLOC |
-                       HASE_DESYNC_START))
+                       HASE_DESYNC_START | HASE_EXPORT_CENTRAL))
         return fail(nullptr, HASE_EINVAL, "unknown flags 0x%x", cfg->flags);
     if (cfg->chunk_steps != 0 && (cfg->chunk_steps < 1 || cfg->chunk_steps > (uint32_t)kMaxChunk))
         return fail(nullptr, HASE_EINVAL, "chunk_steps outside 1..%d", kMaxChunk);
@@ -315,6 +320,10 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     h->obs_words = h->obs_off[h->n_envs];
     h->unp_bytes = (h->flags & HASE_EXPORT_UNPACKED) ? h->unp_off[h->n_envs] : 0;
     h->rows_words = rows;
+    // centralized observation: four planes of `side` one-word rows per env
+    h->central_off.assign(h->n_envs + 1, 0);
+    for (uint32_t e = 0; e < h->n_envs; ++e) h->central_off[e + 1] = h->central_off[e] + 4ull * h->env[e].side;
+    h->central_words = (h->flags & HASE_EXPORT_CENTRAL) ? h->central_off[h->n_envs] : 0;
     if (h->obs_words > 0xffffffffull || h->agents > 0xffffffffull || h->unp_bytes > 0xffffffffull) {
         delete h;
         return fail(nullptr, HASE_EINVAL, "per-step output slice exceeds 2^32 entries");
@@ -376,6 +385,10 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     HASE_ALLOC(h->d_done, R * h->n_envs);
     if (h->flags & HASE_EXPORT_ACTIONS) HASE_ALLOC(h->d_act, R * h->agents);
     if (h->flags & HASE_EXPORT_UNPACKED) HASE_ALLOC(h->d_unp, R * h->unp_bytes);
+    if (h->flags & HASE_EXPORT_CENTRAL) {
+        HASE_ALLOC(h->d_central, 8 * R * h->central_words);
+        HASE_ALLOC(h->d_coff, 4 * h->n_envs);
+    }
     HASE_ALLOC(h->d_err, 4);
     HASE_ALLOC(h->d_thr, 4 * h->n_envs);
     HASE_ALLOC(h->d_clock, 8);
@@ -435,6 +448,20 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
                                    h->d_unp ? h->d_unp + last * h->unp_bytes : nullptr, st),
                     "observe")) != HASE_OK)
         return s;
+    if (h->d_central) {
+        std::vector<uint32_t> coff(h->n_envs);
+        for (uint32_t e = 0; e < h->n_envs; ++e) coff[e] = (uint32_t)h->central_off[e];
+        if ((s = finish(cudaMemsetAsync(h->d_central, 0, 8 * R * h->central_words, st), "memset")) != HASE_OK)
+            return s;
+        if ((s = finish(cudaMemcpyAsync(h->d_coff, coff.data(), 4 * h->n_envs, cudaMemcpyHostToDevice, st),
+                        "copy central offsets")) != HASE_OK)
+            return s;
+        if ((s = finish(cudaStreamSynchronize(st), "central offsets")) != HASE_OK) return s;  // coff is local
+        if ((s = finish(launch_central_init(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_coff,
+                                            h->d_central + last * h->central_words, st),
+                        "central")) != HASE_OK)
+            return s;
+    }
     if (h->flags & HASE_ASYNC_CREATE) {  // the generation flag is read by hase_sync / hase_digest
         *out = h;
         return HASE_OK;
@@ -465,6 +492,9 @@ hase_status hase_reset(hase_handle* h, void* stream) {
     if (h->d_act) HASE_CUDA(h, cudaMemsetAsync(h->d_act + last * h->agents, 0, h->agents, st));
     HASE_CUDA(h, launch_observe(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_obs + last * h->obs_words,
                                 h->d_unp ? h->d_unp + last * h->unp_bytes : nullptr, st));
+    if (h->d_central)
+        HASE_CUDA(h, launch_central_init(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_coff,
+                                         h->d_central + last * h->central_words, st));
     HASE_CUDA(h, cudaMemsetAsync(h->d_clock, 0, 8, st));
     h->t = 0;
     return HASE_OK;
@@ -490,6 +520,9 @@ static hase_status enqueue_steps(hase_handle* h, uint32_t n_steps, cudaStream_t 
         p.done = h->d_done;
         p.act_out = h->d_act;
         p.unp = h->d_unp;
+        p.central = h->d_central;
+        p.central_off = h->d_coff;
+        p.central_words = h->central_words;
         p.obs_words = h->obs_words;
         p.agents = h->agents;
         p.unp_bytes = h->unp_bytes;
@@ -579,6 +612,12 @@ hase_status hase_done_ptr(hase_handle* h, uint8_t** done) {
     return HASE_OK;
 }
 
+hase_status hase_central_ptr(hase_handle* h, uint64_t** central) {
+    if (!h || !central) return fail(h, HASE_EINVAL, "NULL argument");
+    *central = h->d_central;
+    return HASE_OK;
+}
+
 hase_status hase_actions_ptr(hase_handle* h, uint8_t** actions) {
     if (!h || !actions) return fail(h, HASE_EINVAL, "NULL argument");
     *actions = h->d_act;
@@ -595,6 +634,8 @@ hase_status hase_layout_get(hase_handle* h, hase_layout* out) {
     out->agent_off = h->agent_off.data();
     out->obs_off = h->obs_off.data();
     out->unp_off = h->unp_off.data();
+    out->central_words = h->central_words;
+    out->central_off = h->central_off.data();
     return HASE_OK;
 }
 

@@ -209,6 +209,9 @@ struct StepParams {
     uint8_t* done;       // ring [ring][n_envs]
     uint8_t* act_out;    // ring [ring][agents] or null
     uint8_t* unp;        // ring [ring][unp_bytes] or null
+    uint64_t* central;   // ring [ring][central_words] or null (centralized observation)
+    const uint32_t* central_off;  // per env: first word of its centralized observation
+    uint64_t central_words;
     uint64_t obs_words;
     uint64_t agents;
     uint64_t unp_bytes;

@@ -135,6 +135,23 @@ __global__ void observe_kernel(const EnvRT* __restrict__ env, uint32_t n_envs,
     }
 }
 
+// The centralized observation after create / reset, one thread per env.
+__global__ void central_init_kernel(const EnvRT* __restrict__ env, uint32_t n_envs, const uint16_t* __restrict__ pos,
+                                    const uint64_t* __restrict__ rows, const uint32_t* __restrict__ coff,
+                                    uint64_t* __restrict__ central) {
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_envs) return;
+    const EnvRT E = env[e];
+    central_env(E, rows + E.rows_off, pos + E.agent_off, 6u, central + coff[e]);
+}
+
+cudaError_t launch_central_init(const EnvRT* env, uint32_t n_envs, const uint16_t* pos, const uint64_t* rows,
+                                const uint32_t* coff, uint64_t* central, cudaStream_t st) {
+    if (n_envs == 0) return cudaSuccess;
+    central_init_kernel<<<(n_envs + 63) / 64, 64, 0, st>>>(env, n_envs, pos, rows, coff, central);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------------------
 // Launchers (host).
 // --------------------------------------------------------------------------

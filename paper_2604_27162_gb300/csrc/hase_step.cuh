@@ -105,6 +105,67 @@ __device__ inline void window_visibility(uint64_t lo, uint64_t hi, int r, uint64
     }
 }
 
+// Centralized observation of one env (Section 3.3, observability mode 3):
+// four planes over the grid, S rows of one word each (S <= 64) -- 0 cells
+// inside some observing agent's window (with line of sight: visible to it),
+// 1 seen obstacles, 2 seen seekers, 3 seen hiders; bit x of row y is cell
+// (x, y).  src holds the agents' cells packed x | y << sh; rows are the env's
+// padded obstacle rows.
+__device__ inline void central_env(const EnvRT& E, const uint64_t* rows, const uint16_t* src, uint32_t sh,
+                                   uint64_t* out) {
+    const int S = E.side, A = E.n_agents, ns = E.n_seekers, rw = E.rw;
+    const uint32_t xmask = (1u << sh) - 1u;
+    const uint64_t smask = S == 64 ? ~0ull : ((1ull << S) - 1ull);
+    const bool los = line_of_sight(E);
+    uint64_t vl[kMaxAgents], vh[kMaxAgents];  // visible cells of each window (line of sight)
+    if (los) {
+        for (int a = 0; a < A; ++a) {
+            const int team = a < ns ? 0 : 1;
+            vl[a] = vh[a] = 0;
+            if (!team_emits(E, team)) continue;
+            const uint32_t v = src[a] & 0x0fffu;
+            const int r = team_radius(E, team);
+            uint64_t lo, hi;
+            obstacle_plane(rows, rw, (int)(v & xmask), (int)(v >> sh), r, lo, hi);
+            window_visibility(lo, hi, r, vl[a], vh[a]);
+        }
+    }
+    for (int y = 0; y < S; ++y) {
+        uint64_t seen = 0, sk = 0, hd = 0;
+        for (int a = 0; a < A; ++a) {
+            const uint32_t v = src[a] & 0x0fffu;
+            const int xa = (int)(v & xmask), ya = (int)(v >> sh);
+            if (ya == y) {
+                if (a < ns)
+                    sk |= 1ull << xa;
+                else
+                    hd |= 1ull << xa;
+            }
+            const int team = a < ns ? 0 : 1;
+            if (!team_emits(E, team)) continue;
+            const int R = team_radius(E, team), D = 2 * R + 1;
+            const int dy = y - ya;
+            if (dy < -R || dy > R) continue;
+            uint64_t wrow = (1ull << D) - 1ull;
+            if (los) {  // row dy of the window's visible cells
+                const int off = (dy + R) * D;
+                const uint64_t bits = off >= 64 ? vh[a] >> (off - 64)
+                                                : (vl[a] >> off) | (off + D > 64 ? vh[a] << (64 - off) : 0ull);
+                wrow &= bits;
+            }
+            const int x0 = xa - R;
+            seen |= x0 >= 0 ? (wrow << x0) : (wrow >> (-x0));
+        }
+        seen &= smask;
+        const uint64_t* pr = rows + (y + kPad) * rw;
+        const uint64_t obst = (rw == 1 ? (pr[0] >> kPad) : ((pr[0] >> kPad) | (pr[1] << (64 - kPad)))) & smask;
+        out[y] = seen;
+        out[S + y] = seen & obst;
+        out[2 * S + y] = seen & sk;
+        out[3 * S + y] = seen & hd;
+    }
+}
+
 // Ally / opponent planes of agent a from the packed positions P[0..A)
 // (pairwise; used for small groups and by the step -1 observation).
 __device__ __forceinline__ void team_planes_pairwise(int x, int y, int r, int a, int A, int ns,
@@ -141,6 +202,7 @@ struct SlotRec {
 struct CtaShared {
     EnvRT env[kMaxGroupEnvs];
     uint32_t gidx[kMaxGroupEnvs];  // handle env index (done byte, counters)
+    uint32_t coff[kMaxGroupEnvs];  // first word of the env's centralized observation
     GroupPlan plan;
     SlotRec slot[kMaxGroupSlots];
     uint16_t p0[kMaxGroupSlots];  // pristine start cells (CTA packing)
@@ -576,7 +638,7 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
     const uint32_t KP = R * D + R;
     const uint32_t centre = ~shl_clamp(1u, KP), centre_hi = ~shl_clamp(1u, KP - 32u);
     constexpr int first = TA ? NS : 0, end = TA ? A : NS;
-    if (W2) {  // two words a plane: six words an observer, three 16-byte stores
+    if constexpr (W2) {  // two words a plane: six words an observer, three 16-byte stores
 #pragma unroll 1
         for (int a = first; a < end; ++a) {
             const Words3 p =
@@ -596,35 +658,36 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
                 o[5] = p.oph;
             }
         }
-        return;
-    }
+    } else {
 #pragma unroll 1
-    for (int a = first; a < end;) {
-        const Words3 p = observer_words<A, TA, HI, W2>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
-        const int w = 3 * (a - T.ai0);
-        uint64_t* o = T.ob + w;
-        if (!T.emits) {
-            ++a;
-        } else if (T.v16 && !(w & 1) && a + 1 < end) {
-            const Words3 q = observer_words<A, TA, HI, W2>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4,
-                                                       P8, seenf);
-            st16(o, p.o0, p.al);
-            st16(o + 2, p.op, q.o0);
-            st16(o + 4, q.al, q.op);
-            a += 2;
-        } else if (T.v16 && (w & 1)) {
-            o[0] = p.o0;
-            st16(o + 1, p.al, p.op);
-            ++a;
-        } else if (T.v16) {
-            st16(o, p.o0, p.al);
-            o[2] = p.op;
-            ++a;
-        } else {
-            o[0] = p.o0;
-            o[1] = p.al;
-            o[2] = p.op;
-            ++a;
+        for (int a = first; a < end;) {
+            const Words3 p =
+                observer_words<A, TA, HI, W2>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
+            const int w = 3 * (a - T.ai0);
+            uint64_t* o = T.ob + w;
+            if (!T.emits) {
+                ++a;
+            } else if (T.v16 && !(w & 1) && a + 1 < end) {
+                const Words3 q = observer_words<A, TA, HI, W2>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4,
+                                                               P4, P8, seenf);
+                st16(o, p.o0, p.al);
+                st16(o + 2, p.op, q.o0);
+                st16(o + 4, q.al, q.op);
+                a += 2;
+            } else if (T.v16 && (w & 1)) {
+                o[0] = p.o0;
+                st16(o + 1, p.al, p.op);
+                ++a;
+            } else if (T.v16) {
+                st16(o, p.o0, p.al);
+                o[2] = p.op;
+                ++a;
+            } else {
+                o[0] = p.o0;
+                o[1] = p.al;
+                o[2] = p.op;
+                ++a;
+            }
         }
     }
 }
@@ -783,6 +846,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             const EnvRT E = P.env[g];
             H.env[i] = E;
             H.gidx[i] = g;
+            H.coff[i] = P.central ? P.central_off[g] : 0u;
             uint32_t urel = E.unp_off;
             for (int a = 0; a < E.n_agents; ++a) {
                 const int t = a < E.n_seekers ? 0 : 1;
@@ -1065,6 +1129,19 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                     emit_chunk<3>(P, H, C, warp - n_dyn, M, lane);
                 else
                     emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
+            }
+            if (P.central) {  // centralized observations of the chunk's (step, env)s
+                const uint32_t ne_ = (uint32_t)ne;
+                for (uint32_t it = (uint32_t)worker; it < C.len * ne_; it += (uint32_t)n_workers) {
+                    const uint32_t k = it / ne_, e = it - k * ne_;
+                    const int first = L.first_slot[e];
+                    const uint16_t* Tk = C.T + k * nsl + first;
+                    const uint16_t* src = (Tk[0] & kDoneBit) ? H.p0 + first : Tk;
+                    uint32_t sl = C.base_slot + k;
+                    if (sl >= P.ring) sl -= P.ring;
+                    central_env(H.env[e], C.rows + L.rows_off[e], src, cell_shift(H.env[e]),
+                                P.central + (uint64_t)sl * P.central_words + H.coff[e]);
+                }
             }
         }
         // a1 for chunk c + 1

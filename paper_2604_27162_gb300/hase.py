@@ -25,6 +25,8 @@ HASE_EXPORT_UNPACKED = 2
 HASE_ASYNC_CREATE = 4
 HASE_POOL_ALLOC = 8
 HASE_DESYNC_START = 16
+HASE_EXPORT_CENTRAL = 32
+HASE_OBS_LOS = 4
 HASE_OBS_SEEKERS = 1
 HASE_OBS_HIDERS = 2
 STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA",
@@ -34,7 +36,7 @@ STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA
 EXPORTS = [
     "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_digest", "hase_digest_noalloc",
     "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
-    "hase_actions_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
+    "hase_actions_ptr", "hase_central_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
     "hase_get_world", "hase_sync", "hase_launch_info", "hase_destroy", "hase_last_error",
     "hase_request_bytes", "hase_serve",
 ]
@@ -129,6 +131,8 @@ class hase_layout(C.Structure):
         ("agent_off", C.POINTER(C.c_uint64)),
         ("obs_off", C.POINTER(C.c_uint64)),
         ("unp_off", C.POINTER(C.c_uint64)),
+        ("central_words", C.c_uint64),
+        ("central_off", C.POINTER(C.c_uint64)),
     ]
 
 
@@ -159,6 +163,7 @@ def load(path=LIB_PATH):
     L.hase_reward_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_done_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_actions_ptr.argtypes = [H, C.POINTER(P)]
+    L.hase_central_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_layout_get.argtypes = [H, C.POINTER(hase_layout)]
     L.hase_step_count.argtypes = [H, C.POINTER(u64)]
     L.hase_get_state.argtypes = [H, P, C.POINTER(C.c_size_t), P]
@@ -297,6 +302,12 @@ def hase_actions_ptr(h):
     return a.value
 
 
+def hase_central_ptr(h):
+    a = C.c_void_p()
+    _check(load().hase_central_ptr(h, C.byref(a)), h)
+    return a.value
+
+
 def hase_layout_get(h):
     lay = hase_layout()
     _check(load().hase_layout_get(h, C.byref(lay)), h)
@@ -310,6 +321,8 @@ def hase_layout_get(h):
         "agent_off": np.ctypeslib.as_array(lay.agent_off, shape=(n,)).copy(),
         "obs_off": np.ctypeslib.as_array(lay.obs_off, shape=(n,)).copy(),
         "unp_off": np.ctypeslib.as_array(lay.unp_off, shape=(n,)).copy(),
+        "central_words": lay.central_words,
+        "central_off": np.ctypeslib.as_array(lay.central_off, shape=(n,)).copy(),
     }
 
 
@@ -399,6 +412,8 @@ class Engine:
         act = hase_actions_ptr(self.h)
         self.actions = device_view(act, (ring_steps, L["agents"]), "u8", self) if act else None
         self.unpacked = device_view(unp, (ring_steps, L["unp_bytes"]), "u8", self) if unp else None
+        cen = hase_central_ptr(self.h)
+        self.central = device_view(cen, (ring_steps, L["central_words"]), "i64", self) if cen else None
 
     def slot(self, t):
         """Ring slot of global step t (t = -1: the observation after create/reset)."""

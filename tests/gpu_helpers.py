@@ -21,6 +21,8 @@ def engine_outputs(eng):
         out["action"] = eng.actions.cpu().numpy()
     if eng.unpacked is not None:
         out["unpacked"] = eng.unpacked.cpu().numpy()
+    if eng.central is not None:
+        out["central"] = eng.central.cpu().numpy().view(np.uint64)
     return out
 
 
@@ -51,12 +53,16 @@ def compare_run(n_envs, seed, descs, n_steps, ring=None, flags=hase.HASE_EXPORT_
         if unpacked:
             assert (got["unpacked"][ring - 1] == init[1]).all(), "initial unpacked"
         assert (got["reward"][ring - 1] == 0).all() and (got["done"][ring - 1] == 0).all()
+        if "central" in got:
+            assert (got["central"][ring - 1] == w.central()).all(), "initial centralized observation"
     for t in range(n_steps):
         o = w.step(unpacked=unpacked)
+        if "central" in got:
+            o["central"] = w.central()
         if t < n_steps - ring:
             continue
         s = t % ring
-        for k in ("obs", "reward", "done", "action", "unpacked"):
+        for k in ("obs", "reward", "done", "action", "unpacked", "central"):
             if k in got and k in o:
                 if not (got[k][s] == o[k]).all():
                     bad = np.flatnonzero(got[k][s] != o[k])[:8]

@@ -42,7 +42,7 @@ def _grid(c):
 def test_hand_cases_cover_every_rule():
     names = [c["name"] for c in _cases()]
     assert {"obs_inside", "obs_corner", "obs_radius4_two_words", "obs_line_of_sight", "moves",
-            "rewards"} <= set(names)
+            "rewards", "central"} <= set(names)
     assert all("cite" in c for c in _cases())
 
 
@@ -99,3 +99,47 @@ def test_line_of_sight_properties():
     # cells outside the grid block the view beyond them
     assert not oracle.visible(S, empty, 0, 5, -2, 0)
     assert oracle.visible(S, empty, 0, 5, -1, 0)
+
+
+def test_centralized_observation():
+    c = [c for c in _cases() if c["name"] == "central"][0]
+    S, grid = _grid(c)
+    x, y = _xy(c["agents"])
+    r = int(c["radius"])
+    got = oracle.central_one(S, grid, int(c["seekers"]), r, r, 3, x, y)
+    for p in range(4):
+        assert [int(v) for v in got[p, :, 0]] == [int(v) for v in c["plane%d" % p].split()], p
+
+
+def test_centralized_observation_properties():
+    """Seen = the union of the observing agents' windows (without line of
+    sight); seen obstacles and agents are the map's restricted to it; with
+    line of sight the seen plane only shrinks."""
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        S = int(rng.integers(3, 20))
+        grid = (rng.random(S * S) < 0.25).astype(np.uint8)
+        A = int(rng.integers(1, 7))
+        cells = rng.choice(S * S, size=A, replace=False)
+        x, y = cells % S, cells // S
+        ns, rs, rh, teams = int(rng.integers(0, A + 1)), int(rng.integers(0, 4)), int(rng.integers(0, 4)), int(rng.integers(0, 4))
+        c = oracle.central_one(S, grid, ns, rs, rh, teams, x, y)
+        seen = np.zeros((S, S), bool)
+        for a in range(A):
+            team = 0 if a < ns else 1
+            if not (teams >> team) & 1:
+                continue
+            r = rs if team == 0 else rh
+            seen[max(0, y[a] - r):y[a] + r + 1, max(0, x[a] - r):x[a] + r + 1] = True
+        bits = lambda p: np.array([[(int(c[p, yy, xx // 64]) >> (xx % 64)) & 1 for xx in range(S)]
+                                   for yy in range(S)], bool)
+        assert np.array_equal(bits(0), seen)
+        assert np.array_equal(bits(1), seen & grid.reshape(S, S).astype(bool))
+        occ_s = np.zeros((S, S), bool)
+        occ_h = np.zeros((S, S), bool)
+        for a in range(A):
+            (occ_s if a < ns else occ_h)[y[a], x[a]] = True
+        assert np.array_equal(bits(2), seen & occ_s) and np.array_equal(bits(3), seen & occ_h)
+        cl = oracle.central_one(S, grid, ns, rs, rh, teams | 4, x, y)
+        assert not (bits(0) < np.array([[(int(cl[0, yy, xx // 64]) >> (xx % 64)) & 1 for xx in range(S)]
+                                         for yy in range(S)], bool)).any()

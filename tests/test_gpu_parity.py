@@ -114,6 +114,21 @@ def test_line_of_sight_matches_oracle(desc):
     compare_run(20, 18, [desc], 40, smem_cap=32768)  # windows computed without tables
 
 
+@pytest.mark.parametrize("desc", [
+    W.env_desc(32, 10, 5, 3, 2, 40, "0.2"),            # both teams observe
+    W.env_desc(64, 6, 3, 4, 1, 40, "0.2"),             # 64 columns: full-word rows
+    W.env_desc(9, 4, 2, 2, 3, 20, "0.3", 1),           # seekers only
+    W.env_desc(16, 8, 4, 3, 3, 25, "0.25", 3 | 4),     # line of sight
+    W.env_desc(12, 5, 2, 0, 1, 30, "0.2", 2),          # hiders only, radius 0
+])
+def test_centralized_observation_matches_oracle(desc):
+    compare_run(24, 23, [desc], 50, flags=hase.HASE_EXPORT_CENTRAL | hase.HASE_EXPORT_ACTIONS)
+
+
+def test_centralized_observation_uneven():
+    compare_run(30, 24, W.uneven_descs(30, 12), 45, flags=hase.HASE_EXPORT_CENTRAL, launches=[20, 25])
+
+
 def test_line_of_sight_uneven():
     descs = [dict(d, obs_teams=3 | 4) for d in W.uneven_descs(40, 11)]
     compare_run(40, 19, descs, 60)
