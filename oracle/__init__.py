@@ -78,6 +78,7 @@ def load_library(path):
     L.ho_step.argtypes = [P, P, P, P, P, P]
     L.ho_state.argtypes = [P, P, P, P, P, P, P, P]
     L.ho_grid.argtypes = [P, u32, P]
+    L.ho_true_state.argtypes = [P, P, P]
     L.ho_set_state.argtypes = [P, P, P, P, P, u64]
     L.ho_run_digest.argtypes = [P, u64, P, P, P]
     L.ho_splitmix64.argtypes = [u64]
@@ -235,6 +236,14 @@ class World:
         out = np.zeros(max(1, int(self._L.ho_central_words(self._h))), np.uint64)
         self._L.ho_central(self._h, _p(out))
         return out[: int(self._L.ho_central_words(self._h))]
+
+    def true_state(self):
+        """True state of the current step (Sec. 3.3, modes 2, 4, 5): every
+        agent's cell x | y << 6 and every env's episode clock."""
+        cells = np.zeros(max(1, self.n_agents_total), np.uint16)
+        ep_t = np.zeros(max(1, self.n_envs), np.uint32)
+        self._L.ho_true_state(self._h, _p(cells), _p(ep_t))
+        return cells[: self.n_agents_total], ep_t[: self.n_envs]
 
     def state(self):
         n = self.n_agents_total

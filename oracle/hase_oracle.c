@@ -13,7 +13,9 @@
  *              and rewards.
  *   Sec. 3.2   "Collision Models": blocking tiles are impassable.
  *   Sec. 3.3   observability mode 1, "Decentralized Observation (No State)":
- *              each agent sees only its own sight window.
+ *              each agent sees only its own sight window; modes 2-5 add the
+ *              centralized observation and the true state (ho_central,
+ *              ho_true_state).
  *   Sec. 4.1   random actions are generated inside the step (1/3 to 1/2 of
  *              the paper's runtime).
  *   Sec. 4.2   pristine-grid templating: a reset restores the immutable
@@ -601,6 +603,17 @@ void ho_state(const ho_world *w, int32_t *x, int32_t *y, int32_t *sx, int32_t *s
         if (ep_idx) ep_idx[e] = w->ep_idx[e];
     }
     if (t) *t = w->t;
+}
+
+/* True-state record (Sec. 3.3, observability modes 2, 4 and 5: the
+ * environment also returns the omniscient game state).  The dynamic part of
+ * the state: every agent's cell, x | y << 6, agents in handle order, and
+ * every env's episode clock; the static part (obstacles, start cells) is
+ * read with ho_grid / ho_state. */
+void ho_true_state(const ho_world *w, uint16_t *cells, uint32_t *ep_t) {
+    uint64_t n = w->agent_off[w->n_envs];
+    for (uint64_t i = 0; i < n; ++i) cells[i] = (uint16_t)((uint32_t)w->x[i] | ((uint32_t)w->y[i] << 6));
+    for (uint32_t e = 0; e < w->n_envs; ++e) ep_t[e] = w->ep_t[e];
 }
 
 void ho_grid(const ho_world *w, uint32_t e, uint8_t *out) {

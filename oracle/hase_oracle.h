@@ -136,6 +136,9 @@ void ho_state(const ho_world *w, int32_t *x, int32_t *y, int32_t *sx, int32_t *s
               uint32_t *ep_t, uint32_t *ep_idx, uint64_t *t);
 
 /* Obstacle grid of env e (side*side bytes, row-major). */
+/* True state of the current step (Sec. 3.3, modes 2, 4, 5): cells[agent] =
+ * x | y << 6, ep_t[env] = steps into the current episode. */
+void ho_true_state(const ho_world *w, uint16_t *cells, uint32_t *ep_t);
 void ho_grid(const ho_world *w, uint32_t e, uint8_t *out);
 
 /* Overwrite the dynamic state (positions, counters, t).  Used by tests that

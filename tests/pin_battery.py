@@ -181,6 +181,71 @@ def _run(L):
     return all((st0[k] == s1[k]).all() for k in ("x", "y", "ep_t", "ep_idx"))
 
 
+def _modes(L):
+    """Line of sight, the centralized observation, the desynchronised start
+    and the true state (the hand-worked cases of tests/golden and their
+    properties)."""
+    from tests.test_golden_hand_cases import _cases, _grid, _xy
+
+    cases = {c["name"]: c for c in _cases()}
+    c = cases["obs_line_of_sight"]
+    S, grid = _grid(c)
+    x, y = _xy(c["agents"])
+    got = oracle.observe_agent(S, grid, int(c["seekers"]), x, y, int(c["observer"]), int(c["radius"]), 1,
+                               L=L, los=True)
+    if [int(got[p, 0]) for p in range(3)] != [int(c["plane%d" % p]) for p in range(3)]:
+        return False
+    for name in ("central", "central_seekers_only"):
+        c = cases[name]
+        S, grid = _grid(c)
+        x, y = _xy(c["agents"])
+        r = int(c["radius"])
+        got = oracle.central_one(S, grid, int(c["seekers"]), r, r, int(c.get("teams", "3")), x, y, L=L)
+        for p in range(4):
+            if [int(v) for v in got[p, :, 0]] != [int(v) for v in c["plane%d" % p].split()]:
+                return False
+    # desynchronised start: offset floor(u cap / 2^32), u = word 0 of Philox
+    # counter (0, 0, env, 3); the first episode ends after cap - offset steps
+    cap, n, seed = 9, 12, 77
+    w = oracle.World(n, seed, [W.env_desc(8, 2, 1, 1, 1, cap, "0.1")], L=L, desync=True)
+    key = (seed & 0xffffffff, seed >> 32)
+    want = [(int(oracle.philox4x32_10((0, 0, e, 3), key, L=L)[0]) * cap) >> 32 for e in range(n)]
+    if [int(v) for v in w.state()["ep_t"]] != want:
+        return False
+    first = [None] * n
+    for t in range(cap):
+        d = w.step()["done"]
+        for e in range(n):
+            if d[e] and first[e] is None:
+                first[e] = t + 1
+    if first != [cap - v for v in want]:
+        return False
+    # true state: the hand case, and the full-view centralized planes
+    c = cases["true_state"]
+    x, y = _xy(c["agents"])
+    w = oracle.World(1, 1, [W.env_desc(int(c["side"]), len(x), int(c["seekers"]), 1, 1, 100, 0)], L=L)
+    w.set_state(x, y, [int(c["ep_t"])], [0], 0)
+    cells, ep = w.true_state()
+    if [int(v) for v in cells] != [int(v) for v in c["cells"].split()] or int(ep[0]) != int(c["ep_t"]):
+        return False
+    w = oracle.World(2, 4, [W.env_desc(4, 5, 3, 4, 4, 5, "0.2")], L=L)
+    for k in range(1, 8):
+        w.step()
+        cells, ep = w.true_state()
+        cen = w.central()
+        if [int(v) for v in ep] != [k % 5] * 2:
+            return False
+        for e in range(2):
+            pl = cen[e * 16:(e + 1) * 16].reshape(4, 4)
+            occ = [[0] * 4 for _ in range(2)]
+            for a in range(5):
+                v = int(cells[e * 5 + a])
+                occ[0 if a < 3 else 1][v >> 6] |= 1 << (v & 63)
+            if [int(v) for v in pl[2]] != occ[0] or [int(v) for v in pl[3]] != occ[1]:
+                return False
+    return True
+
+
 CHECKS = {
     "philox": None,
     "actions": _actions,
@@ -189,6 +254,7 @@ CHECKS = {
     "observations": _observations,
     "generation": _generation,
     "run": _run,
+    "modes": _modes,
 }
 
 

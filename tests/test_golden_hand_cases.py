@@ -42,7 +42,7 @@ def _grid(c):
 def test_hand_cases_cover_every_rule():
     names = [c["name"] for c in _cases()]
     assert {"obs_inside", "obs_corner", "obs_radius4_two_words", "obs_line_of_sight", "moves",
-            "rewards", "central"} <= set(names)
+            "rewards", "central", "true_state"} <= set(names)
     assert all("cite" in c for c in _cases())
 
 
@@ -102,13 +102,15 @@ def test_line_of_sight_properties():
 
 
 def test_centralized_observation():
-    c = [c for c in _cases() if c["name"] == "central"][0]
-    S, grid = _grid(c)
-    x, y = _xy(c["agents"])
-    r = int(c["radius"])
-    got = oracle.central_one(S, grid, int(c["seekers"]), r, r, 3, x, y)
-    for p in range(4):
-        assert [int(v) for v in got[p, :, 0]] == [int(v) for v in c["plane%d" % p].split()], p
+    for c in _cases():
+        if not c["name"].startswith("central"):
+            continue
+        S, grid = _grid(c)
+        x, y = _xy(c["agents"])
+        r = int(c["radius"])
+        got = oracle.central_one(S, grid, int(c["seekers"]), r, r, int(c.get("teams", "3")), x, y)
+        for p in range(4):
+            assert [int(v) for v in got[p, :, 0]] == [int(v) for v in c["plane%d" % p].split()], (c["name"], p)
 
 
 def test_centralized_observation_properties():
@@ -143,3 +145,47 @@ def test_centralized_observation_properties():
         cl = oracle.central_one(S, grid, ns, rs, rh, teams | 4, x, y)
         assert not (bits(0) < np.array([[(int(cl[0, yy, xx // 64]) >> (xx % 64)) & 1 for xx in range(S)]
                                          for yy in range(S)], bool)).any()
+
+
+def test_true_state_record():
+    from paper_2604_27162_gb300 import workloads as W
+
+    c = [c for c in _cases() if c["name"] == "true_state"][0]
+    x, y = _xy(c["agents"])
+    w = oracle.World(1, 1, [W.env_desc(int(c["side"]), len(x), int(c["seekers"]), 1, 1, 100, 0)])
+    w.set_state(x, y, [int(c["ep_t"])], [0], 0)
+    cells, ep_t = w.true_state()
+    assert [int(v) for v in cells] == [int(v) for v in c["cells"].split()]
+    assert [int(v) for v in ep_t] == [int(c["ep_t"])]
+
+
+def test_true_state_against_full_view_central():
+    """With radius 4 on a 4x4 grid every window covers the grid, so the
+    centralized seeker and hider planes are exactly the true state's cells;
+    the episode clock after k steps is k mod cap."""
+    from paper_2604_27162_gb300 import workloads as W
+
+    cap = 7
+    descs = [W.env_desc(4, A, (A + 1) // 2, 4, 4, cap, "0.2") for A in (1, 3, 5, 6)]
+    w = oracle.World(4, 9, descs)
+    off = np.concatenate([[0], np.cumsum([d["n_agents"] for d in descs])])
+    for k in range(1, 20):
+        w.step()
+        cells, ep_t = w.true_state()
+        cen = w.central()
+        assert [int(v) for v in ep_t] == [k % cap] * 4
+        for e, d in enumerate(descs):
+            S, ns = d["side"], d["n_seekers"]
+            pl = cen[e * 4 * S:(e + 1) * 4 * S].reshape(4, S)
+            sk = np.zeros(S, np.uint64)
+            hd = np.zeros(S, np.uint64)
+            for a in range(d["n_agents"]):
+                v = int(cells[off[e] + a])
+                cx, cy = v & 63, v >> 6
+                assert 0 <= cx < S and 0 <= cy < S
+                if a < ns:
+                    sk[cy] |= np.uint64(1 << cx)
+                else:
+                    hd[cy] |= np.uint64(1 << cx)
+            assert np.array_equal(pl[0], np.full(S, (1 << S) - 1, np.uint64))
+            assert np.array_equal(pl[2], sk) and np.array_equal(pl[3], hd)

@@ -52,6 +52,13 @@ MUTANTS = [
     ("start duplicates allowed", "if (cells[b] == cell) dup = 1;", ";"),
     ("obstacle word index", "g[c] = out[c % 4u] < p->density_thr ? 1 : 0;",
      "g[c] = out[0] < p->density_thr ? 1 : 0;"),
+    ("line of sight rounds down", "return p >= 0 ? (2 * p + n) / (2 * n) : -((-2 * p + n) / (2 * n));",
+     "return p >= 0 ? p / n : -((-p) / n);"),
+    ("central ignores observing teams", "                if (!((obs_teams >> team) & 1u)) continue;\n                const int32_t r = (int32_t)(team ? r_hide : r_seek);",
+     "                const int32_t r = (int32_t)(team ? r_hide : r_seek);"),
+    ("desync offset word", "return mulhi32(out[0], w->env[e].cap);", "return mulhi32(out[1], w->env[e].cap);"),
+    ("true state x and y transposed", "cells[i] = (uint16_t)((uint32_t)w->x[i] | ((uint32_t)w->y[i] << 6));",
+     "cells[i] = (uint16_t)((uint32_t)w->y[i] | ((uint32_t)w->x[i] << 6));"),
 ]
 
 
