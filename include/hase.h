@@ -42,6 +42,10 @@
  *                                (only with HASE_EXPORT_UNPACKED)
  *   central  uint64 [central_words] env e at central_off[e]: [4][S]
  *                                (only with HASE_EXPORT_CENTRAL)
+ *   cells    uint16 [agents]     env e at agent_off[e]: the cell x | y << 6
+ *                                of every agent (only with HASE_EXPORT_STATE)
+ *   ep_t     uint32 [n_envs]     steps into the current episode
+ *                                (only with HASE_EXPORT_STATE)
  * A_obs(e) counts the agents whose team emits observations (seekers first).
  * Pointers returned by the *_ptr calls stay valid until hase_destroy; their
  * contents are valid once the stream work that wrote them has completed.
@@ -95,6 +99,18 @@ typedef enum hase_status {
                                 /* at floor(u * cap / 2^32), u = word 0 of   */
                                 /* Philox counter (0, 0, env, 3), at create  */
                                 /* and at every hase_reset                   */
+#define HASE_EXPORT_STATE 64u  /* also write the true state [Sec. 3.3,      */
+                                /* modes 2, 4, 5]: after every step the cell */
+                                /* of every agent and the episode clock of   */
+                                /* every env (the observed state: on a done  */
+                                /* step, the reset one)                      */
+#define HASE_SKIP_OBS 128u      /* write no decentralized observation        */
+                                /* (obs_words = 0) [Sec. 3.3, modes 3-6];    */
+                                /* obs_teams still chooses whose sightlines  */
+                                /* feed HASE_EXPORT_CENTRAL.  Modes: 1 none, */
+                                /* 2 EXPORT_STATE, 3 SKIP_OBS|EXPORT_CENTRAL,*/
+                                /* 4 3 + EXPORT_STATE, 5 SKIP_OBS|EXPORT_    */
+                                /* STATE, 6 SKIP_OBS (rewards and done only) */
 #define HASE_POOL_ALLOC 8u      /* buffers from the device's stream-ordered  */
                                 /* pool (allocated on the create stream,     */
                                 /* returned by hase_destroy on the stream of */
@@ -111,8 +127,9 @@ typedef enum hase_status {
                             /* unseen cells read 0 in all three planes           */
 
 /* One environment's parameters.  Seekers are agents 0..n_seekers-1, hiders
- * n_seekers..n_agents-1.  obs_teams = 0 writes no observation (the paper's
- * "void output" mode). */
+ * n_seekers..n_agents-1.  obs_teams = 0 writes no observation and feeds no
+ * centralized one (with no HASE_EXPORT_STATE: the paper's "void output"
+ * mode). */
 typedef struct hase_env_desc {
     uint32_t side;        /* grid side S, 2..HASE_MAX_SIDE                   */
     uint32_t n_agents;    /* A, 1..HASE_MAX_AGENTS, A <= S*S                 */
@@ -190,6 +207,9 @@ hase_status hase_reward_ptr(hase_handle *h, int32_t **reward);
 hase_status hase_done_ptr(hase_handle *h, uint8_t **done);
 hase_status hase_actions_ptr(hase_handle *h, uint8_t **actions);
 hase_status hase_central_ptr(hase_handle *h, uint64_t **central);
+/* The true-state rings (HASE_EXPORT_STATE; NULL without it): cells
+ * [ring_steps][agents] and ep_t [ring_steps][n_envs]. */
+hase_status hase_state_ptr(hase_handle *h, uint16_t **cells, uint32_t **ep_t);
 hase_status hase_layout_get(hase_handle *h, hase_layout *out);
 
 /* The same n_steps as one CUDA graph: the first call for a given n_steps

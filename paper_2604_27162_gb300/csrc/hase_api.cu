@@ -25,6 +25,8 @@ cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint
 cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st);
 cudaError_t launch_central_init(const EnvRT* env, uint32_t n_envs, const uint16_t* pos, const uint64_t* rows,
                                 const uint32_t* coff, uint64_t* central, cudaStream_t st);
+cudaError_t launch_state_init(const uint16_t* pos, const EnvState* est, uint32_t agents, uint32_t n_envs,
+                              uint16_t* cells, uint32_t* ept, cudaStream_t st);
 cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
                           uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
                           uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
@@ -47,6 +49,8 @@ struct hase_handle {
     uint64_t central_words = 0;
     uint64_t* d_central = nullptr;
     uint32_t* d_coff = nullptr;
+    uint16_t* d_cells = nullptr;  // true state rings (HASE_EXPORT_STATE)
+    uint32_t* d_ept = nullptr;
     uint64_t agents = 0, obs_words = 0, unp_bytes = 0, rows_words = 0;
     uint32_t smem = 0, threads = 0, kc = 16, emit_warps = 0, steps_per_launch = 0, n_dyn = 1;
     uint32_t smem_budget = kSmemBudget;
@@ -110,7 +114,7 @@ static hase_status cuda_fail(hase_handle* h, cudaError_t e, const char* what) {
 static void free_all(hase_handle* h) {
     void* ptrs[] = {h->d_env, h->d_est,  h->d_pos, h->d_start, h->d_rows, h->d_groups,
                     h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr, h->d_env_list,
-                    h->d_clock, h->d_scratch, h->d_central, h->d_coff};
+                    h->d_clock, h->d_scratch, h->d_central, h->d_coff, h->d_cells, h->d_ept};
     const bool pool = h->flags & HASE_POOL_ALLOC;
     for (void* p : ptrs)
         if (p) {
@@ -250,8 +254,10 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if ((uint64_t)cfg->env_id_base + cfg->n_envs > 0x100000000ull)
         return fail(nullptr, HASE_EINVAL, "env ids exceed 32 bits");
     if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED | HASE_ASYNC_CREATE | HASE_POOL_ALLOC |
-                       HASE_DESYNC_START | HASE_EXPORT_CENTRAL))
+                       HASE_DESYNC_START | HASE_EXPORT_CENTRAL | HASE_EXPORT_STATE | HASE_SKIP_OBS))
         return fail(nullptr, HASE_EINVAL, "unknown flags 0x%x", cfg->flags);
+    if ((cfg->flags & HASE_SKIP_OBS) && (cfg->flags & HASE_EXPORT_UNPACKED))
+        return fail(nullptr, HASE_EINVAL, "HASE_EXPORT_UNPACKED needs the decentralized observation");
     if (cfg->chunk_steps != 0 && (cfg->chunk_steps < 1 || cfg->chunk_steps > (uint32_t)kMaxChunk))
         return fail(nullptr, HASE_EINVAL, "chunk_steps outside 1..%d", kMaxChunk);
     if (cfg->emit_warps > 12) return fail(nullptr, HASE_EINVAL, "emit_warps outside 1..12");
@@ -287,8 +293,9 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         const hase_env_desc& d = cfg->envs[cfg->n_desc == 1 ? 0 : e];
         uint32_t wmax = 0, n_obs = 0;
         uint64_t unp = 0;
+        const bool skip_obs = (cfg->flags & HASE_SKIP_OBS) != 0u;
         for (uint32_t a = 0; a < d.n_agents; ++a) {
-            if (!emits(d, a)) continue;
+            if (skip_obs || !emits(d, a)) continue;
             const uint32_t D = 2 * radius(d, a) + 1;
             wmax = std::max(wmax, (D * D + 63) / 64);
             n_obs += 1;
@@ -300,7 +307,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         E.n_seekers = (uint8_t)d.n_seekers;
         E.r_seek = (uint8_t)d.r_seek;
         E.r_hide = (uint8_t)d.r_hide;
-        E.obs_teams = (uint8_t)d.obs_teams;
+        E.obs_teams = (uint8_t)(d.obs_teams | (skip_obs ? kObsNoDec : 0u));
         E.wpp = (uint8_t)wmax;
         E.rw = (uint8_t)((d.side + 2 * kPad <= 64) ? 1 : 2);
         E.cap = d.cap;
@@ -389,6 +396,10 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         HASE_ALLOC(h->d_central, 8 * R * h->central_words);
         HASE_ALLOC(h->d_coff, 4 * h->n_envs);
     }
+    if (h->flags & HASE_EXPORT_STATE) {
+        HASE_ALLOC(h->d_cells, 2 * R * h->agents);
+        HASE_ALLOC(h->d_ept, 4 * R * h->n_envs);
+    }
     HASE_ALLOC(h->d_err, 4);
     HASE_ALLOC(h->d_thr, 4 * h->n_envs);
     HASE_ALLOC(h->d_clock, 8);
@@ -439,6 +450,10 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         return s;
     if (h->d_unp && (s = finish(cudaMemsetAsync(h->d_unp, 0, R * h->unp_bytes, st), "memset")) != HASE_OK)
         return s;
+    if (h->d_cells && (s = finish(cudaMemsetAsync(h->d_cells, 0, 2 * R * h->agents, st), "memset")) != HASE_OK)
+        return s;
+    if (h->d_ept && (s = finish(cudaMemsetAsync(h->d_ept, 0, 4 * R * h->n_envs, st), "memset")) != HASE_OK)
+        return s;
     const uint32_t key0 = (uint32_t)(h->seed & 0xffffffffu), key1 = (uint32_t)(h->seed >> 32);
     if ((s = finish(launch_generate(h->d_env, h->d_thr, h->n_envs, key0, key1, h->d_pos, h->d_start, h->d_rows,
                                     h->d_err, st), "generate")) != HASE_OK)
@@ -447,6 +462,11 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if ((s = finish(launch_observe(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_obs + last * h->obs_words,
                                    h->d_unp ? h->d_unp + last * h->unp_bytes : nullptr, st),
                     "observe")) != HASE_OK)
+        return s;
+    if (h->d_cells && (s = finish(launch_state_init(h->d_pos, h->d_est, (uint32_t)h->agents, h->n_envs,
+                                                    h->d_cells + last * h->agents, h->d_ept + last * h->n_envs,
+                                                    st),
+                                  "true state")) != HASE_OK)
         return s;
     if (h->d_central) {
         std::vector<uint32_t> coff(h->n_envs);
@@ -495,6 +515,9 @@ hase_status hase_reset(hase_handle* h, void* stream) {
     if (h->d_central)
         HASE_CUDA(h, launch_central_init(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_coff,
                                          h->d_central + last * h->central_words, st));
+    if (h->d_cells)
+        HASE_CUDA(h, launch_state_init(h->d_pos, h->d_est, (uint32_t)h->agents, h->n_envs,
+                                       h->d_cells + last * h->agents, h->d_ept + last * h->n_envs, st));
     HASE_CUDA(h, cudaMemsetAsync(h->d_clock, 0, 8, st));
     h->t = 0;
     return HASE_OK;
@@ -523,6 +546,8 @@ static hase_status enqueue_steps(hase_handle* h, uint32_t n_steps, cudaStream_t 
         p.central = h->d_central;
         p.central_off = h->d_coff;
         p.central_words = h->central_words;
+        p.st_cells = h->d_cells;
+        p.st_ept = h->d_ept;
         p.obs_words = h->obs_words;
         p.agents = h->agents;
         p.unp_bytes = h->unp_bytes;
@@ -615,6 +640,13 @@ hase_status hase_done_ptr(hase_handle* h, uint8_t** done) {
 hase_status hase_central_ptr(hase_handle* h, uint64_t** central) {
     if (!h || !central) return fail(h, HASE_EINVAL, "NULL argument");
     *central = h->d_central;
+    return HASE_OK;
+}
+
+hase_status hase_state_ptr(hase_handle* h, uint16_t** cells, uint32_t** ep_t) {
+    if (!h || !cells || !ep_t) return fail(h, HASE_EINVAL, "NULL argument");
+    *cells = h->d_cells;
+    *ep_t = h->d_ept;
     return HASE_OK;
 }
 

@@ -28,6 +28,7 @@ constexpr int kMaxDyn = 4;            // dynamics warps per CTA
 constexpr int kMaxChunk = 64;         // steps per on-chip chunk
 constexpr int kObsHiders = 2;         // obs_teams value: only hiders emit
 constexpr uint32_t kObsLos = 4;       // obs_teams bit: line of sight masks the windows
+constexpr uint32_t kObsNoDec = 8;     // obs_teams bit: no decentralized planes are written
 constexpr uint32_t kDoneBit = 0x8000u;
 constexpr uint32_t kOccBit = 0x80u;   // occupancy bit of the neighbour map
 constexpr uint32_t kSmemBudget = 216 * 1024;  // dynamic shared memory per CTA
@@ -69,7 +70,12 @@ struct Group {
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
-__host__ __device__ inline bool team_emits(const EnvRT& E, int team) { return (E.obs_teams >> team) & 1u; }
+// team_sees: the team's sightlines feed the centralized observation;
+// team_emits: the team also writes decentralized planes.
+__host__ __device__ inline bool team_sees(const EnvRT& E, int team) { return (E.obs_teams >> team) & 1u; }
+__host__ __device__ inline bool team_emits(const EnvRT& E, int team) {
+    return team_sees(E, team) && !(E.obs_teams & kObsNoDec);
+}
 __host__ __device__ inline bool only_hiders_emit(const EnvRT& E) { return (E.obs_teams & 3u) == (uint32_t)kObsHiders; }
 __host__ __device__ inline bool line_of_sight(const EnvRT& E) { return (E.obs_teams & kObsLos) != 0u; }
 __host__ __device__ inline int team_radius(const EnvRT& E, int team) { return team ? E.r_hide : E.r_seek; }
@@ -211,6 +217,8 @@ struct StepParams {
     uint8_t* unp;        // ring [ring][unp_bytes] or null
     uint64_t* central;   // ring [ring][central_words] or null (centralized observation)
     const uint32_t* central_off;  // per env: first word of its centralized observation
+    uint16_t* st_cells;  // ring [ring][agents] or null (true state: cells x | y << 6)
+    uint32_t* st_ept;    // ring [ring][n_envs] or null (true state: episode clocks)
     uint64_t central_words;
     uint64_t obs_words;
     uint64_t agents;

@@ -3,7 +3,9 @@
 //
 //   gen_kernel      a0: start cells and Bernoulli obstacle rows (Sec. 3.2,
 //                   Sec. 4.2 pristine template), one warp per env
-//   observe_kernel  the step -1 observation after create / reset
+//   observe_kernel  the step -1 observation after create / reset (and
+//                   central_init_kernel, state_init_kernel: its centralized
+//                   observation and true state)
 //   digest kernels  the run summary of hase_digest / hase_digest_noalloc
 //   advance_kernel  the device step counter
 // and the host launchers; the step kernel itself is in hase_step.cuh.
@@ -149,6 +151,24 @@ cudaError_t launch_central_init(const EnvRT* env, uint32_t n_envs, const uint16_
                                 const uint32_t* coff, uint64_t* central, cudaStream_t st) {
     if (n_envs == 0) return cudaSuccess;
     central_init_kernel<<<(n_envs + 63) / 64, 64, 0, st>>>(env, n_envs, pos, rows, coff, central);
+    return cudaGetLastError();
+}
+
+// The true state after create / reset: the cells (the handle's positions are
+// already x | y << 6) and the episode clocks, one thread per agent or env.
+__global__ void state_init_kernel(const uint16_t* __restrict__ pos, const EnvState* __restrict__ est,
+                                  uint32_t agents, uint32_t n_envs, uint16_t* __restrict__ cells,
+                                  uint32_t* __restrict__ ept) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < agents) cells[i] = pos[i];
+    if (i < n_envs) ept[i] = est[i].ep_t;
+}
+
+cudaError_t launch_state_init(const uint16_t* pos, const EnvState* est, uint32_t agents, uint32_t n_envs,
+                              uint16_t* cells, uint32_t* ept, cudaStream_t st) {
+    const uint32_t n = agents > n_envs ? agents : n_envs;
+    if (n == 0) return cudaSuccess;
+    state_init_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, est, agents, n_envs, cells, ept);
     return cudaGetLastError();
 }
 

@@ -122,7 +122,7 @@ __device__ inline void central_env(const EnvRT& E, const uint64_t* rows, const u
         for (int a = 0; a < A; ++a) {
             const int team = a < ns ? 0 : 1;
             vl[a] = vh[a] = 0;
-            if (!team_emits(E, team)) continue;
+            if (!team_sees(E, team)) continue;
             const uint32_t v = src[a] & 0x0fffu;
             const int r = team_radius(E, team);
             uint64_t lo, hi;
@@ -142,7 +142,7 @@ __device__ inline void central_env(const EnvRT& E, const uint64_t* rows, const u
                     hd |= 1ull << xa;
             }
             const int team = a < ns ? 0 : 1;
-            if (!team_emits(E, team)) continue;
+            if (!team_sees(E, team)) continue;
             const int R = team_radius(E, team), D = 2 * R + 1;
             const int dy = y - ya;
             if (dy < -R || dy > R) continue;
@@ -203,6 +203,7 @@ struct CtaShared {
     EnvRT env[kMaxGroupEnvs];
     uint32_t gidx[kMaxGroupEnvs];  // handle env index (done byte, counters)
     uint32_t coff[kMaxGroupEnvs];  // first word of the env's centralized observation
+    uint32_t ept0[kMaxGroupEnvs];  // episode clock before the launch's first step
     GroupPlan plan;
     SlotRec slot[kMaxGroupSlots];
     uint16_t p0[kMaxGroupSlots];  // pristine start cells (CTA packing)
@@ -227,12 +228,13 @@ struct EmitCtx {
     const uint64_t* tbl;    // obstacle-window tables
     uint32_t len;           // steps in the chunk
     uint32_t base_slot;     // ring slot of the chunk's first step
+    uint32_t k0;            // steps of the launch before the chunk
     int worker, n_workers;  // this thread among the emission threads
 };
 
 // ---------------------------------------------------------------------------
 // General emission (a5, a6, a9), for groups outside the one-thread form
-// below (windows over 64 bits, or seekers other than ceil(A/2)): one lane per
+// below (line of sight, or seekers other than ceil(A/2)): one lane per
 // agent of a (step, env).  Each lane tests every other agent against its own
 // window (radius of its team) and sets the bit in the plane of that agent's
 // team; the reward's "seen" test (seeker radius) is combined over the
@@ -487,7 +489,7 @@ struct TeamCtx {
     const SlotRec* slot;  // slot records of the env's agents
     uint32_t sh, xmask, side, rw;
     int ai0;              // emitting index of agent 0 of the team base
-    bool emits, use_table;
+    bool use_table;
     bool v16;             // the env's obs words start 16-byte aligned
 };
 
@@ -595,7 +597,7 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
     w.oph = op2;
     w.o0 = 0;
     w.o0h = 0;
-    if (T.emits) {  // a5 obstacle plane
+    {  // a5 obstacle plane
         if (T.use_table) {
             if (W2 && R == 4u) {  // two table words a cell
                 const uint64_t* c = T.tbl + 2u * (ya * T.side + xa);
@@ -643,7 +645,6 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
         for (int a = first; a < end; ++a) {
             const Words3 p =
                 observer_words<A, TA, HI, W2>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
-            if (!T.emits) continue;
             uint64_t* o = T.ob + 6 * (a - T.ai0);
             if (T.v16) {
                 st16(o, p.o0, p.o0h);
@@ -665,9 +666,7 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
                 observer_words<A, TA, HI, W2>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
             const int w = 3 * (a - T.ai0);
             uint64_t* o = T.ob + w;
-            if (!T.emits) {
-                ++a;
-            } else if (T.v16 && !(w & 1) && a + 1 < end) {
+            if (T.v16 && !(w & 1) && a + 1 < end) {
                 const Words3 q = observer_words<A, TA, HI, W2>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4,
                                                                P4, P8, seenf);
                 st16(o, p.o0, p.al);
@@ -705,64 +704,66 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
     const bool done = (Tk[0] & kDoneBit) != 0u;
     const uint16_t* src = done ? (H.p0 + first) : Tk;  // observed positions
     const uint32_t rs = E.r_seek, rh = E.r_hide, Ds = 2u * rs + 1u, Dh = 2u * rh + 1u;
+    uint32_t sl = C.base_slot + k;
+    if (sl >= P.ring) sl -= P.ring;
+    const bool emit_s = team_emits(E, 0), emit_h = A > 1 && team_emits(E, 1);
     uint32_t X4[NW], Y4[NW], Ps[NW], Ph[NW], seenf[NW];
 #pragma unroll
     for (int j = 0; j < NW; ++j) X4[j] = Y4[j] = Ps[j] = Ph[j] = seenf[j] = 0u;
+    if (emit_s || emit_h) {
 #pragma unroll
-    for (int b = 0; b < A; ++b) {
-        const uint32_t v = src[b] & 0x0fffu;
-        const uint32_t x = v & xmask, y = v >> sh;
-        const int j = b >> 2, s8 = 8 * (b & 3);
-        X4[j] |= x << s8;
-        Y4[j] |= y << s8;
-        Ps[j] |= ((y * Ds + x) & 0xffu) << s8;
-        Ph[j] |= ((y * Dh + x) & 0xffu) << s8;
-    }
-    uint32_t Ps8[NW], Ph8[NW];
+        for (int b = 0; b < A; ++b) {
+            const uint32_t v = src[b] & 0x0fffu;
+            const uint32_t x = v & xmask, y = v >> sh;
+            const int j = b >> 2, s8 = 8 * (b & 3);
+            X4[j] |= x << s8;
+            Y4[j] |= y << s8;
+            Ps[j] |= ((y * Ds + x) & 0xffu) << s8;
+            Ph[j] |= ((y * Dh + x) & 0xffu) << s8;
+        }
+        uint32_t Ps8[NW], Ph8[NW];
 #pragma unroll
-    for (int j = 0; j < NW; ++j) {
-        Ps8[j] = Ps[j] & 0x80808080u;
-        Ps[j] &= 0x7f7f7f7fu;
-        Ph8[j] = Ph[j] & 0x80808080u;
-        Ph[j] &= 0x7f7f7f7fu;
-    }
-    uint32_t sl = C.base_slot + k;
-    if (sl >= P.ring) sl -= P.ring;
-    const bool emit_s = team_emits(E, 0), emit_h = team_emits(E, 1);
-    TeamCtx T;
-    T.src = src;
-    T.rows = C.rows + L.rows_off[e];
-    T.ob = P.obs + (uint64_t)sl * P.obs_words + E.obs_off;
-    T.unp = P.unp ? P.unp + (uint64_t)sl * P.unp_bytes : nullptr;
-    T.slot = H.slot + first;
-    T.sh = sh;
-    T.xmask = xmask;
-    T.side = E.side;
-    T.rw = E.rw;
-    T.use_table = L.flags & kUseTable;
-    T.v16 = (reinterpret_cast<uintptr_t>(T.ob) & 15u) == 0u;
-    T.tbl = C.tbl + L.tbl_off[e][0];
-    T.ai0 = 0;
-    T.emits = emit_s;
-    if (W2)
-        emit_team_fast<A, false, true, true>(T, rs, X4, Y4, Ps, Ps8, seenf);
-    else if (Ds * Ds > 32u)
-        emit_team_fast<A, false, true, false>(T, rs, X4, Y4, Ps, Ps8, seenf);
-    else
-        emit_team_fast<A, false, false, false>(T, rs, X4, Y4, Ps, Ps8, seenf);
-    if (A > 1 && emit_h) {
-        T.tbl = C.tbl + L.tbl_off[e][1];
-        T.ai0 = emit_s ? 0 : NS;
-        T.emits = true;
-        if (W2)
-            emit_team_fast<A, true, true, true>(T, rh, X4, Y4, Ph, Ph8, seenf);
-        else if (Dh * Dh > 32u)
-            emit_team_fast<A, true, true, false>(T, rh, X4, Y4, Ph, Ph8, seenf);
-        else
-            emit_team_fast<A, true, false, false>(T, rh, X4, Y4, Ph, Ph8, seenf);
+        for (int j = 0; j < NW; ++j) {
+            Ps8[j] = Ps[j] & 0x80808080u;
+            Ps[j] &= 0x7f7f7f7fu;
+            Ph8[j] = Ph[j] & 0x80808080u;
+            Ph[j] &= 0x7f7f7f7fu;
+        }
+        TeamCtx T;
+        T.src = src;
+        T.rows = C.rows + L.rows_off[e];
+        T.ob = P.obs + (uint64_t)sl * P.obs_words + E.obs_off;
+        T.unp = P.unp ? P.unp + (uint64_t)sl * P.unp_bytes : nullptr;
+        T.slot = H.slot + first;
+        T.sh = sh;
+        T.xmask = xmask;
+        T.side = E.side;
+        T.rw = E.rw;
+        T.use_table = L.flags & kUseTable;
+        T.v16 = (reinterpret_cast<uintptr_t>(T.ob) & 15u) == 0u;
+        T.tbl = C.tbl + L.tbl_off[e][0];
+        T.ai0 = 0;
+        if (emit_s) {
+            if (W2)
+                emit_team_fast<A, false, true, true>(T, rs, X4, Y4, Ps, Ps8, seenf);
+            else if (Ds * Ds > 32u)
+                emit_team_fast<A, false, true, false>(T, rs, X4, Y4, Ps, Ps8, seenf);
+            else
+                emit_team_fast<A, false, false, false>(T, rs, X4, Y4, Ps, Ps8, seenf);
+        }
+        if (emit_h) {
+            T.tbl = C.tbl + L.tbl_off[e][1];
+            T.ai0 = emit_s ? 0 : NS;
+            if (W2)
+                emit_team_fast<A, true, true, true>(T, rh, X4, Y4, Ph, Ph8, seenf);
+            else if (Dh * Dh > 32u)
+                emit_team_fast<A, true, true, false>(T, rh, X4, Y4, Ph, Ph8, seenf);
+            else
+                emit_team_fast<A, true, false, false>(T, rh, X4, Y4, Ph, Ph8, seenf);
+        }
     }
     uint32_t seen = 0;
-    if (done) {
+    if (done || !emit_s) {  // the reward's test straight from the positions
         seen = seen_pre_reset(Tk, A, NS, (int)rs, sh);
     } else {
 #pragma unroll
@@ -847,6 +848,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             H.env[i] = E;
             H.gidx[i] = g;
             H.coff[i] = P.central ? P.central_off[g] : 0u;
+            H.ept0[i] = P.st_ept ? P.est[g].ep_t : 0u;
             uint32_t urel = E.unp_off;
             for (int a = 0; a < E.n_agents; ++a) {
                 const int t = a < E.n_seekers ? 0 : 1;
@@ -1120,6 +1122,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             C.rows = s_rows;
             C.tbl = s_tbl;
             C.base_slot = (uint32_t)((T0 + (uint64_t)cp * kc) % P.ring);
+            C.k0 = cp * kc;
             C.worker = worker;
             C.n_workers = n_workers;
             if constexpr (FAM > 0) {
@@ -1130,17 +1133,26 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                 else
                     emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
             }
-            if (P.central) {  // centralized observations of the chunk's (step, env)s
+            if (P.central || P.st_cells) {  // centralized observation, true state
                 const uint32_t ne_ = (uint32_t)ne;
                 for (uint32_t it = (uint32_t)worker; it < C.len * ne_; it += (uint32_t)n_workers) {
                     const uint32_t k = it / ne_, e = it - k * ne_;
                     const int first = L.first_slot[e];
                     const uint16_t* Tk = C.T + k * nsl + first;
                     const uint16_t* src = (Tk[0] & kDoneBit) ? H.p0 + first : Tk;
+                    const EnvRT& E = H.env[e];
+                    const uint32_t sh = cell_shift(E);
                     uint32_t sl = C.base_slot + k;
                     if (sl >= P.ring) sl -= P.ring;
-                    central_env(H.env[e], C.rows + L.rows_off[e], src, cell_shift(H.env[e]),
-                                P.central + (uint64_t)sl * P.central_words + H.coff[e]);
+                    if (P.central)
+                        central_env(E, C.rows + L.rows_off[e], src, sh,
+                                    P.central + (uint64_t)sl * P.central_words + H.coff[e]);
+                    if (P.st_cells) {  // the observed state: cells and the episode clock after the step
+                        uint16_t* cl = P.st_cells + (uint64_t)sl * P.agents + E.agent_off;
+                        for (int b = 0; b < E.n_agents; ++b) cl[b] = (uint16_t)to_hbm(src[b] & 0x0fffu, sh);
+                        P.st_ept[(uint64_t)sl * P.n_envs + H.gidx[e]] =
+                            (uint32_t)(((uint64_t)H.ept0[e] + C.k0 + k + 1u) % E.cap);
+                    }
                 }
             }
         }

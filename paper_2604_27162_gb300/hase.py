@@ -26,6 +26,8 @@ HASE_ASYNC_CREATE = 4
 HASE_POOL_ALLOC = 8
 HASE_DESYNC_START = 16
 HASE_EXPORT_CENTRAL = 32
+HASE_EXPORT_STATE = 64
+HASE_SKIP_OBS = 128
 HASE_OBS_LOS = 4
 HASE_OBS_SEEKERS = 1
 HASE_OBS_HIDERS = 2
@@ -36,7 +38,7 @@ STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA
 EXPORTS = [
     "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_digest", "hase_digest_noalloc",
     "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
-    "hase_actions_ptr", "hase_central_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
+    "hase_actions_ptr", "hase_central_ptr", "hase_state_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
     "hase_get_world", "hase_sync", "hase_launch_info", "hase_destroy", "hase_last_error",
     "hase_request_bytes", "hase_serve",
 ]
@@ -164,6 +166,7 @@ def load(path=LIB_PATH):
     L.hase_done_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_actions_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_central_ptr.argtypes = [H, C.POINTER(P)]
+    L.hase_state_ptr.argtypes = [H, C.POINTER(P), C.POINTER(P)]
     L.hase_layout_get.argtypes = [H, C.POINTER(hase_layout)]
     L.hase_step_count.argtypes = [H, C.POINTER(u64)]
     L.hase_get_state.argtypes = [H, P, C.POINTER(C.c_size_t), P]
@@ -308,6 +311,13 @@ def hase_central_ptr(h):
     return a.value
 
 
+def hase_state_ptr(h):
+    """(cells, ep_t) device pointers of the true-state rings, or (None, None)."""
+    a, b = C.c_void_p(), C.c_void_p()
+    _check(load().hase_state_ptr(h, C.byref(a), C.byref(b)), h)
+    return a.value, b.value
+
+
 def hase_layout_get(h):
     lay = hase_layout()
     _check(load().hase_layout_get(h, C.byref(lay)), h)
@@ -386,9 +396,9 @@ def device_view(ptr, shape, dtype, owner=None):
     """torch tensor aliasing device memory at ptr (no copy)."""
     import torch
 
-    typestr = {"u8": "|u1", "i32": "<i4", "i64": "<i8", "u16": "<u2"}[dtype]
+    typestr = {"u8": "|u1", "i16": "<i2", "i32": "<i4", "i64": "<i8"}[dtype]
     if int(np.prod(shape)) == 0:
-        tdt = {"u8": torch.uint8, "i32": torch.int32, "i64": torch.int64, "u16": torch.uint16}[dtype]
+        tdt = {"u8": torch.uint8, "i16": torch.int16, "i32": torch.int32, "i64": torch.int64}[dtype]
         return torch.empty(shape, dtype=tdt, device="cuda")
     return torch.as_tensor(_DeviceArray(ptr, shape, typestr, owner), device="cuda")
 
@@ -414,6 +424,10 @@ class Engine:
         self.unpacked = device_view(unp, (ring_steps, L["unp_bytes"]), "u8", self) if unp else None
         cen = hase_central_ptr(self.h)
         self.central = device_view(cen, (ring_steps, L["central_words"]), "i64", self) if cen else None
+        # true state: cells x | y << 6 (<= 4095) and episode clocks (< 2^31)
+        cells, ept = hase_state_ptr(self.h)
+        self.cells = device_view(cells, (ring_steps, L["agents"]), "i16", self) if cells else None
+        self.ep_t = device_view(ept, (ring_steps, n_envs), "i32", self) if ept else None
 
     def slot(self, t):
         """Ring slot of global step t (t = -1: the observation after create/reset)."""

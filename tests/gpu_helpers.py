@@ -23,6 +23,9 @@ def engine_outputs(eng):
         out["unpacked"] = eng.unpacked.cpu().numpy()
     if eng.central is not None:
         out["central"] = eng.central.cpu().numpy().view(np.uint64)
+    if eng.cells is not None:
+        out["cells"] = eng.cells.cpu().numpy().view(np.uint16)
+        out["ep_t"] = eng.ep_t.cpu().numpy().view(np.uint32)
     return out
 
 
@@ -43,26 +46,35 @@ def compare_run(n_envs, seed, descs, n_steps, ring=None, flags=hase.HASE_EXPORT_
             total += item
     assert total == n_steps
     got = engine_outputs(eng)
+    if flags & hase.HASE_SKIP_OBS:  # no decentralized observation at all
+        assert got["obs"].shape == (ring, 0), got["obs"].shape
+        del got["obs"]
     unpacked = bool(flags & hase.HASE_EXPORT_UNPACKED)
     w = oracle.World(n_envs, seed, descs, env_id_base=env_id_base,
                      desync=bool(flags & hase.HASE_DESYNC_START))
     if ring > n_steps:
         init = w.observe(unpacked=unpacked)
         o0 = init[0] if unpacked else init
-        assert (got["obs"][ring - 1] == o0).all(), "initial observation"
+        assert "obs" not in got or (got["obs"][ring - 1] == o0).all(), "initial observation"
         if unpacked:
             assert (got["unpacked"][ring - 1] == init[1]).all(), "initial unpacked"
         assert (got["reward"][ring - 1] == 0).all() and (got["done"][ring - 1] == 0).all()
         if "central" in got:
             assert (got["central"][ring - 1] == w.central()).all(), "initial centralized observation"
+        if "cells" in got:
+            cells, ep_t = w.true_state()
+            assert (got["cells"][ring - 1] == cells).all(), "initial true state (cells)"
+            assert (got["ep_t"][ring - 1] == ep_t).all(), "initial true state (episode clocks)"
     for t in range(n_steps):
         o = w.step(unpacked=unpacked)
         if "central" in got:
             o["central"] = w.central()
+        if "cells" in got:
+            o["cells"], o["ep_t"] = w.true_state()
         if t < n_steps - ring:
             continue
         s = t % ring
-        for k in ("obs", "reward", "done", "action", "unpacked", "central"):
+        for k in ("obs", "reward", "done", "action", "unpacked", "central", "cells", "ep_t"):
             if k in got and k in o:
                 if not (got[k][s] == o[k]).all():
                     bad = np.flatnonzero(got[k][s] != o[k])[:8]

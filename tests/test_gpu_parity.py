@@ -134,6 +134,42 @@ def test_line_of_sight_uneven():
     compare_run(40, 19, descs, 60)
 
 
+# Observability modes of Section 3.3 (mode 1 is the default everywhere else).
+MODES = {
+    2: hase.HASE_EXPORT_STATE,
+    3: hase.HASE_SKIP_OBS | hase.HASE_EXPORT_CENTRAL,
+    4: hase.HASE_SKIP_OBS | hase.HASE_EXPORT_CENTRAL | hase.HASE_EXPORT_STATE,
+    5: hase.HASE_SKIP_OBS | hase.HASE_EXPORT_STATE,
+    6: hase.HASE_SKIP_OBS,
+}
+
+
+@pytest.mark.parametrize("mode", sorted(MODES))
+@pytest.mark.parametrize("desc", [
+    W.env_desc(32, 10, 5, 3, 2, 40, "0.2"),            # one-thread emission, one word a plane
+    W.env_desc(24, 7, 4, 4, 4, 40, "0.25"),            # one-thread emission, radius 4 (two words)
+    W.env_desc(16, 6, 2, 3, 1, 30, "0.3"),             # lane-per-agent emission
+    W.env_desc(16, 8, 4, 3, 3, 25, "0.25", 3 | 4),     # line of sight
+], ids=["fast", "fast-r4", "lane", "los"])
+def test_observability_modes_match_oracle(mode, desc):
+    compare_run(24, 31, [desc], 70, flags=MODES[mode] | hase.HASE_EXPORT_ACTIONS, launches=[30, 40])
+
+
+def test_true_state_uneven_desynchronised_and_reset():
+    flags = hase.HASE_EXPORT_STATE | hase.HASE_DESYNC_START | hase.HASE_EXPORT_CENTRAL
+    descs = W.uneven_descs(36, 13)
+    compare_run(36, 6, descs, 90, flags=flags, launches=[11, ("graph", 40), 39])
+    compare_run(36, 6, descs, 90, flags=flags | hase.HASE_SKIP_OBS, ring=17, launches=[50, 40])
+    # hase_reset writes the true state of the reset (step -1) again
+    eng = hase.Engine(36, 6, descs, 64, flags)
+    eng.step(70)
+    eng.reset()
+    got = engine_outputs(eng)
+    cells, ep_t = oracle.World(36, 6, descs, desync=True).true_state()
+    assert (got["cells"][63] == cells).all() and (got["ep_t"][63] == ep_t).all()
+    eng.close()
+
+
 def test_ring_wraparound_and_split_launches():
     c = W.ten1k()
     compare_run(64, c["seed"], c["descs"], 300, ring=7, launches=[1, 2, 97, 200])
@@ -213,6 +249,11 @@ def test_invalid_configs_rejected():
         hase.Engine(4, 0, [good], 0)
     with pytest.raises(hase.HaseError):
         hase.Engine(0, 0, [good], 2)
+    with pytest.raises(hase.HaseError) as ei:  # no decentralized planes to unpack
+        hase.Engine(4, 0, [good], 2, hase.HASE_SKIP_OBS | hase.HASE_EXPORT_UNPACKED)
+    assert ei.value.status == hase.HASE_EINVAL
+    with pytest.raises(hase.HaseError):
+        hase.Engine(4, 0, [good], 2, 1 << 8)  # unknown flag
 
 
 # ---------------------------------------------------------------------------
