@@ -79,6 +79,13 @@ def load_library(path):
     L.ho_state.argtypes = [P, P, P, P, P, P, P, P]
     L.ho_grid.argtypes = [P, u32, P]
     L.ho_true_state.argtypes = [P, P, P]
+    L.ho_fog_units.argtypes = [u32, u32, u32, u32]
+    L.ho_fog_units.restype = u32
+    L.ho_fog_update.argtypes = [u32, P, u32, u32, u32, u32, u32, u32, P, P, u32, P, P]
+    L.ho_set_fog.argtypes = [P, C.c_int]
+    L.ho_fog_words.argtypes = [P]
+    L.ho_fog_words.restype = u64
+    L.ho_fog.argtypes = [P, P]
     L.ho_set_state.argtypes = [P, P, P, P, P, u64]
     L.ho_run_digest.argtypes = [P, u64, P, P, P]
     L.ho_splitmix64.argtypes = [u64]
@@ -158,6 +165,22 @@ def central_one(S, grid, n_seekers, r_seek, r_hide, obs_teams, x, y, L=None):
     return out.reshape(4, S, rw)
 
 
+def fog_update(S, grid, n_seekers, r_seek, r_hide, obs_teams, per_agent, x, y, start, disc, L=None):
+    """One fog-of-war update of one env (the discovery maps [units][S][S] as
+    uint8, updated in place); returns the newly discovered cells."""
+    L = L or lib()
+    A = len(x)
+    units = int(L.ho_fog_units(A, n_seekers, obs_teams, int(per_agent)))
+    assert disc.shape == (units, S, S) and disc.dtype == np.uint8 and disc.flags["C_CONTIGUOUS"]
+    fresh = np.zeros_like(disc)
+    g = np.ascontiguousarray(grid, np.uint8)
+    xs = np.ascontiguousarray(x, np.int32)
+    ys = np.ascontiguousarray(y, np.int32)
+    L.ho_fog_update(S, _p(g), A, n_seekers, r_seek, r_hide, obs_teams, int(per_agent), _p(xs), _p(ys),
+                    int(start), _p(disc), _p(fresh))
+    return fresh
+
+
 def observe_agent(S, grid, n_seekers, x, y, a, r, W=None, L=None, los=False):
     if W is None:
         W = ((2 * r + 1) ** 2 + 63) // 64
@@ -172,7 +195,7 @@ def observe_agent(S, grid, n_seekers, x, y, a, r, W=None, L=None, los=False):
 class World:
     """A batch of environments stepped by the oracle, outputs as numpy."""
 
-    def __init__(self, n_envs, seed, descs, env_id_base=0, L=None, desync=False):
+    def __init__(self, n_envs, seed, descs, env_id_base=0, L=None, desync=False, fog=0):
         self._L = L or lib()
         self._descs = env_array(descs)
         h = self._L.ho_create(n_envs, env_id_base, seed, C.cast(self._descs, C.c_void_p),
@@ -196,6 +219,8 @@ class World:
                            _p(self.words_per_plane))
         if desync:
             self._L.ho_set_desync(self._h, 1)
+        if fog:  # 1 global, 2 per-agent discovery maps
+            self._L.ho_set_fog(self._h, int(fog))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -236,6 +261,14 @@ class World:
         out = np.zeros(max(1, int(self._L.ho_central_words(self._h))), np.uint64)
         self._L.ho_central(self._h, _p(out))
         return out[: int(self._L.ho_central_words(self._h))]
+
+    def fog(self):
+        """Fog-of-war maps of the current step: per env [units][2][side] rows
+        (discovered, newly discovered)."""
+        n = int(self._L.ho_fog_words(self._h))
+        out = np.zeros(max(1, n), np.uint64)
+        self._L.ho_fog(self._h, _p(out))
+        return out[:n]
 
     def true_state(self):
         """True state of the current step (Sec. 3.3, modes 2, 4, 5): every

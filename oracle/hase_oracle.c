@@ -48,6 +48,9 @@ struct ho_world {
     uint32_t *ep_t;         /* steps into the current episode, per env */
     uint32_t *ep_idx;       /* finished episodes, per env              */
     int desync;             /* episode clocks start at a drawn offset  */
+    int fog;                /* 0 off, 1 global, 2 per-agent discovery  */
+    uint64_t *fog_off;      /* n_envs + 1 (bytes of the fog maps)      */
+    uint8_t *disc, *fresh;  /* discovery maps and their newest cells   */
 };
 
 static char g_err[256];
@@ -283,6 +286,77 @@ void ho_central_one(uint32_t side, const uint8_t *grid, uint32_t A, uint32_t n_s
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Fog of war (Section 3.3 and the observation-layer table of Section 4: a   */
+/* discovery map, per agent or global, where seen cells stay marked -- the   */
+/* paper notes that visibility is monotone, "once seen, always seen"; and    */
+/* the "diff sweep" variant of Section 5, which touches only newly           */
+/* discovered tiles).  Unit j of an env is the j-th observing agent          */
+/* (per_agent) or all observing agents together.                             */
+/* ------------------------------------------------------------------------ */
+uint32_t ho_fog_units(uint32_t A, uint32_t n_seekers, uint32_t obs_teams, uint32_t per_agent) {
+    if (!per_agent) return 1u;
+    uint32_t n = 0;
+    for (uint32_t a = 0; a < A; ++a) {
+        const uint32_t team = a < n_seekers ? 0u : 1u;
+        if ((obs_teams >> team) & 1u) ++n;
+    }
+    return n;
+}
+
+/* Whether agent a sees cell (x, y): inside its (2r+1)^2 window and, with
+ * line of sight, visible from it. */
+static int agent_sees(uint32_t side, const uint8_t *grid, int32_t ax, int32_t ay, int32_t r, uint32_t los,
+                      int32_t x, int32_t y) {
+    const int32_t dx = x - ax, dy = y - ay;
+    if (dx < -r || dx > r || dy < -r || dy > r) return 0;
+    return !los || ho_visible(side, grid, ax, ay, dx, dy);
+}
+
+/* One update of one env's maps (side*side bytes per unit, row major).  A
+ * cell is discovered once some agent of the unit has seen it in the current
+ * episode; an episode's first observation (start != 0: after create, reset
+ * or an auto-reset) begins with an empty map.  fresh marks the cells that
+ * this update discovered. */
+void ho_fog_update(uint32_t side, const uint8_t *grid, uint32_t A, uint32_t n_seekers, uint32_t r_seek,
+                   uint32_t r_hide, uint32_t obs_teams, uint32_t per_agent, const int32_t *ax,
+                   const int32_t *ay, uint32_t start, uint8_t *disc, uint8_t *fresh) {
+    const uint32_t los = (obs_teams >> 2) & 1u;
+    const uint64_t cells = (uint64_t)side * side;
+    const uint32_t units = ho_fog_units(A, n_seekers, obs_teams, per_agent);
+    for (uint32_t u = 0; u < units; ++u) {
+        uint8_t *d = disc + u * cells;
+        uint8_t *f = fresh + u * cells;
+        for (int32_t y = 0; y < (int32_t)side; ++y) {
+            for (int32_t x = 0; x < (int32_t)side; ++x) {
+                int seen = 0;
+                uint32_t k = 0; /* index among the observing agents */
+                for (uint32_t a = 0; a < A && !seen; ++a) {
+                    const uint32_t team = a < n_seekers ? 0u : 1u;
+                    if (!((obs_teams >> team) & 1u)) continue;
+                    const uint32_t mine = !per_agent || k == u;
+                    k += 1;
+                    if (!mine) continue;
+                    const int32_t r = (int32_t)(team ? r_hide : r_seek);
+                    seen = agent_sees(side, grid, ax[a], ay[a], r, los, x, y);
+                }
+                const size_t c = (size_t)y * side + (size_t)x;
+                const uint8_t before = start ? 0 : d[c];
+                d[c] = (uint8_t)(before | seen);
+                f[c] = (uint8_t)(seen && !before);
+            }
+        }
+    }
+}
+
+static void fog_env(ho_world *w, uint32_t e, uint32_t start) {
+    const ho_env *p = &w->env[e];
+    const uint64_t base = w->agent_off[e];
+    ho_fog_update(p->side, w->grid[e], p->n_agents, p->n_seekers, p->r_seek, p->r_hide, p->obs_teams,
+                  w->fog == 2, &w->x[base], &w->y[base], start, w->disc + w->fog_off[e],
+                  w->fresh + w->fog_off[e]);
+}
+
 static void central_env(const ho_world *w, uint32_t e, uint64_t *out) {
     const ho_env *p = &w->env[e];
     const uint64_t base = w->agent_off[e];
@@ -458,6 +532,9 @@ void ho_destroy(ho_world *w) {
     free(w->y);
     free(w->ep_t);
     free(w->ep_idx);
+    free(w->fog_off);
+    free(w->disc);
+    free(w->fresh);
     free(w);
 }
 
@@ -489,6 +566,66 @@ void ho_reset(ho_world *w) {
         for (uint64_t i = w->agent_off[e]; i < w->agent_off[e + 1]; ++i) {
             w->x[i] = w->sx[i];
             w->y[i] = w->sy[i];
+        }
+        if (w->fog) fog_env(w, e, 1u);
+    }
+}
+
+/* Fog-of-war maps on (mode 1 global, 2 per agent) or off (0); restarts the
+ * world like ho_reset, so the maps begin with the first observation. */
+void ho_set_fog(ho_world *w, int mode) {
+    free(w->fog_off);
+    free(w->disc);
+    free(w->fresh);
+    w->fog_off = NULL;
+    w->disc = w->fresh = NULL;
+    w->fog = mode == 1 || mode == 2 ? mode : 0;
+    if (w->fog) {
+        w->fog_off = (uint64_t *)calloc(w->n_envs + 1, sizeof(uint64_t));
+        for (uint32_t e = 0; e < w->n_envs; ++e) {
+            const ho_env *p = &w->env[e];
+            w->fog_off[e + 1] = w->fog_off[e] + (uint64_t)ho_fog_units(p->n_agents, p->n_seekers, p->obs_teams,
+                                                                       w->fog == 2) *
+                                                    p->side * p->side;
+        }
+        const uint64_t n = w->fog_off[w->n_envs];
+        w->disc = (uint8_t *)calloc(n ? n : 1, 1);
+        w->fresh = (uint8_t *)calloc(n ? n : 1, 1);
+    }
+    ho_reset(w);
+}
+
+/* Words of ho_fog: per env [units][2][side][ceil(side / 64)]. */
+uint64_t ho_fog_words(const ho_world *w) {
+    if (!w->fog) return 0;
+    uint64_t n = 0;
+    for (uint32_t e = 0; e < w->n_envs; ++e) {
+        const ho_env *p = &w->env[e];
+        n += (uint64_t)ho_fog_units(p->n_agents, p->n_seekers, p->obs_teams, w->fog == 2) * 2u * p->side *
+             ((p->side + 63u) / 64u);
+    }
+    return n;
+}
+
+/* The maps of the current step, packed: per env and unit the discovery map
+ * then the newly discovered cells, each side rows of bits (bit x of row y
+ * = cell (x, y)). */
+void ho_fog(const ho_world *w, uint64_t *out) {
+    uint64_t o = 0;
+    for (uint32_t e = 0; w->fog && e < w->n_envs; ++e) {
+        const ho_env *p = &w->env[e];
+        const uint32_t S = p->side, rw = (S + 63u) / 64u;
+        const uint32_t units = ho_fog_units(p->n_agents, p->n_seekers, p->obs_teams, w->fog == 2);
+        for (uint32_t u = 0; u < units; ++u) {
+            for (uint32_t q = 0; q < 2; ++q) {
+                const uint8_t *m = (q ? w->fresh : w->disc) + w->fog_off[e] + (uint64_t)u * S * S;
+                for (uint32_t y = 0; y < S; ++y) {
+                    for (uint32_t k = 0; k < rw; ++k) out[o + (uint64_t)y * rw + k] = 0;
+                    for (uint32_t x = 0; x < S; ++x)
+                        if (m[(size_t)y * S + x]) out[o + (uint64_t)y * rw + x / 64] |= (uint64_t)1 << (x % 64);
+                }
+                o += (uint64_t)S * rw;
+            }
         }
     }
 }
@@ -581,6 +718,7 @@ static void step_env(ho_world *w, uint32_t e, uint64_t *obs, int32_t *rew, uint8
     }
     if (done) done[e] = d;
     if (obs || unp) observe_env(w, e, obs, unp);
+    if (w->fog) fog_env(w, e, d != 0);
 }
 
 void ho_step(ho_world *w, uint64_t *obs, int32_t *rew, uint8_t *done, uint8_t *act,

@@ -136,6 +136,22 @@ void ho_state(const ho_world *w, int32_t *x, int32_t *y, int32_t *sx, int32_t *s
               uint32_t *ep_t, uint32_t *ep_idx, uint64_t *t);
 
 /* Obstacle grid of env e (side*side bytes, row-major). */
+/* Fog of war (Sec. 3.3, the discovery-map layer of Sec. 4, the diff sweep
+ * of Sec. 5): unit j of an env is the j-th observing agent (per_agent) or
+ * all observing agents; a cell is discovered once a unit's agent has seen it
+ * in the current episode.  ho_fog_update applies one step to one env's
+ * byte maps ([units][side][side]; start != 0 on an episode's first
+ * observation); ho_set_fog turns the world's maps on (1 global, 2 per agent)
+ * and restarts it; ho_fog packs them per env as [units][2][side] rows
+ * (discovered, newly discovered). */
+uint32_t ho_fog_units(uint32_t A, uint32_t n_seekers, uint32_t obs_teams, uint32_t per_agent);
+void ho_fog_update(uint32_t side, const uint8_t *grid, uint32_t A, uint32_t n_seekers, uint32_t r_seek,
+                   uint32_t r_hide, uint32_t obs_teams, uint32_t per_agent, const int32_t *ax,
+                   const int32_t *ay, uint32_t start, uint8_t *disc, uint8_t *fresh);
+void ho_set_fog(ho_world *w, int mode);
+uint64_t ho_fog_words(const ho_world *w);
+void ho_fog(const ho_world *w, uint64_t *out);
+
 /* True state of the current step (Sec. 3.3, modes 2, 4, 5): cells[agent] =
  * x | y << 6, ep_t[env] = steps into the current episode. */
 void ho_true_state(const ho_world *w, uint16_t *cells, uint32_t *ep_t);

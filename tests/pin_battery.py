@@ -243,6 +243,38 @@ def _modes(L):
                 occ[0 if a < 3 else 1][v >> 6] |= 1 << (v & 63)
             if [int(v) for v in pl[2]] != occ[0] or [int(v) for v in pl[3]] != occ[1]:
                 return False
+    # fog of war: the hand cases, and a run against the centralized views
+    from tests.test_golden_hand_cases import _rows
+
+    c = cases["fog"]
+    S, grid = _grid(c)
+    disc = np.zeros((1, S, S), np.uint8)
+    for k in range(4):
+        start, cl = c["update%d" % k].split(" ", 1)
+        x, y = _xy(cl)
+        fresh = oracle.fog_update(S, grid, 1, 1, 1, 1, False, x, y, int(start), disc, L=L)
+        if _rows(disc[0]) != [int(v) for v in c["disc%d" % k].split()]:
+            return False
+        if _rows(fresh[0]) != [int(v) for v in c["fresh%d" % k].split()]:
+            return False
+    c = cases["fog_per_agent"]
+    S, grid = _grid(c)
+    x, y = _xy(c["agents"])
+    per = np.zeros((2, S, S), np.uint8)
+    oracle.fog_update(S, grid, 1, 1, 1, 3, True, x, y, 1, per, L=L)
+    if _rows(per[0]) != [int(v) for v in c["unit0"].split()] or _rows(per[1]) != [int(v) for v in c["unit1"].split()]:
+        return False
+    d = W.env_desc(9, 4, 2, 2, 1, 5, "0.25", 3)
+    w = oracle.World(1, 8, [d], L=L, fog=1)
+    acc = None
+    for t in range(12):
+        done = w.step()["done"][0] if t else 1
+        seen = w.central()[:9]
+        prev = np.zeros(9, np.uint64) if done else acc
+        acc = prev | seen
+        f = w.fog()
+        if not np.array_equal(f[:9], acc) or not np.array_equal(f[9:], acc & ~prev):
+            return False
     return True
 
 

@@ -42,7 +42,7 @@ def _grid(c):
 def test_hand_cases_cover_every_rule():
     names = [c["name"] for c in _cases()]
     assert {"obs_inside", "obs_corner", "obs_radius4_two_words", "obs_line_of_sight", "moves",
-            "rewards", "central", "true_state"} <= set(names)
+            "rewards", "central", "true_state", "fog", "fog_per_agent"} <= set(names)
     assert all("cite" in c for c in _cases())
 
 
@@ -189,3 +189,35 @@ def test_true_state_against_full_view_central():
                     hd[cy] |= np.uint64(1 << cx)
             assert np.array_equal(pl[0], np.full(S, (1 << S) - 1, np.uint64))
             assert np.array_equal(pl[2], sk) and np.array_equal(pl[3], hd)
+
+
+def _rows(m):
+    """Rows of bits (bit x of row y) of one byte map [S][S]."""
+    return [sum(int(v) << x for x, v in enumerate(row)) for row in m]
+
+
+def test_fog_of_war_updates():
+    c = [c for c in _cases() if c["name"] == "fog"][0]
+    S, grid = _grid(c)
+    r, ns, teams = int(c["radius"]), int(c["seekers"]), int(c["teams"])
+    disc = np.zeros((1, S, S), np.uint8)
+    for k in range(4):
+        start, cells = c["update%d" % k].split(" ", 1)
+        x, y = _xy(cells)
+        fresh = oracle.fog_update(S, grid, ns, r, r, teams, False, x, y, int(start), disc)
+        assert _rows(disc[0]) == [int(v) for v in c["disc%d" % k].split()], k
+        assert _rows(fresh[0]) == [int(v) for v in c["fresh%d" % k].split()], k
+
+
+def test_fog_of_war_per_agent_and_global():
+    c = [c for c in _cases() if c["name"] == "fog_per_agent"][0]
+    S, grid = _grid(c)
+    r, ns, teams = int(c["radius"]), int(c["seekers"]), int(c["teams"])
+    x, y = _xy(c["agents"])
+    per = np.zeros((2, S, S), np.uint8)
+    oracle.fog_update(S, grid, ns, r, r, teams, True, x, y, 1, per)
+    glob = np.zeros((1, S, S), np.uint8)
+    oracle.fog_update(S, grid, ns, r, r, teams, False, x, y, 1, glob)
+    assert _rows(per[0]) == [int(v) for v in c["unit0"].split()]
+    assert _rows(per[1]) == [int(v) for v in c["unit1"].split()]
+    assert _rows(glob[0]) == [int(v) for v in c["global"].split()]

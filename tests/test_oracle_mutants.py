@@ -57,6 +57,11 @@ MUTANTS = [
     ("central ignores observing teams", "                if (!((obs_teams >> team) & 1u)) continue;\n                const int32_t r = (int32_t)(team ? r_hide : r_seek);",
      "                const int32_t r = (int32_t)(team ? r_hide : r_seek);"),
     ("desync offset word", "return mulhi32(out[0], w->env[e].cap);", "return mulhi32(out[1], w->env[e].cap);"),
+    ("fog map kept across episodes", "const uint8_t before = start ? 0 : d[c];", "const uint8_t before = d[c];"),
+    ("fog fresh is the whole map", "f[c] = (uint8_t)(seen && !before);", "f[c] = (uint8_t)(before | seen);"),
+    ("fog per-agent unit ignores its agent", "const uint32_t mine = !per_agent || k == u;",
+     "const uint32_t mine = 1;"),
+    ("fog not updated on steps", "    if (w->fog) fog_env(w, e, d != 0);\n", "\n"),
     ("true state x and y transposed", "cells[i] = (uint16_t)((uint32_t)w->x[i] | ((uint32_t)w->y[i] << 6));",
      "cells[i] = (uint16_t)((uint32_t)w->y[i] | ((uint32_t)w->x[i] << 6));"),
 ]

@@ -489,3 +489,52 @@ def test_desynchronised_start():
     for e in range(n):
         assert ends[e][0] == cap - 1 - ep1[e], e
         assert all(b - a == cap for a, b in zip(ends[e], ends[e][1:])), e
+
+
+def test_fog_of_war_equals_union_of_centralized_views():
+    """The global discovery map is the OR of the centralized observation's
+    seen plane over the episode so far, and the newly discovered plane is
+    its difference to the previous step (the whole map at an episode start);
+    per-agent maps OR to the global one, and each equals the seen plane of
+    a centralized view of that agent alone (line of sight included)."""
+    descs = [W.env_desc(9, 5, 3, 2, 1, 6, "0.25", 3),
+             W.env_desc(12, 4, 2, 3, 2, 5, "0.3", 3 | 4),
+             W.env_desc(7, 3, 1, 0, 2, 4, "0.2", 2),
+             W.env_desc(10, 6, 3, 4, 4, 7, "0.2", 1 | 4)]
+    n = len(descs)
+    glob = oracle.World(n, 21, descs, fog=1)
+    per = oracle.World(n, 21, descs, fog=2)
+    grids = [glob.grid(e) for e in range(n)]
+    acc = [None] * n
+    done = np.ones(n, np.uint8)  # step -1 starts every episode
+    for t in range(-1, 16):
+        if t >= 0:
+            done = glob.step()["done"]
+            per.step()
+        cen, fg, fp = glob.central(), glob.fog(), per.fog()
+        st = glob.state()
+        co = fo = po = ao = 0
+        for e, d in enumerate(descs):
+            S, A, ns = d["side"], d["n_agents"], d["n_seekers"]
+            seen = cen[co:co + S]
+            prev = np.zeros(S, np.uint64) if done[e] else acc[e]
+            acc[e] = prev | seen
+            assert np.array_equal(fg[fo:fo + S], acc[e]), (t, e)
+            assert np.array_equal(fg[fo + S:fo + 2 * S], acc[e] & ~prev), (t, e)
+            obs = [a for a in range(A) if (d["obs_teams"] >> (0 if a < ns else 1)) & 1]
+            union = np.zeros(S, np.uint64)
+            for j, a in enumerate(obs):
+                m = fp[po + 2 * j * S:po + (2 * j + 1) * S]
+                union |= m
+                one = oracle.central_one(S, grids[e].reshape(-1), 1 if a < ns else 0, d["r_seek"], d["r_hide"],
+                                         d["obs_teams"], st["x"][ao + a:ao + a + 1], st["y"][ao + a:ao + a + 1])
+                if done[e]:
+                    assert np.array_equal(m, one[0, :, 0]), (t, e, a)
+                else:
+                    assert not (one[0, :, 0] & ~m).any(), (t, e, a)  # this step's view is discovered
+            assert np.array_equal(union, acc[e]), (t, e)
+            co += 4 * S
+            fo += 2 * S
+            po += 2 * S * len(obs)
+            ao += A
+    assert (st["ep_idx"] > 0).all()  # every env went through an auto-reset
