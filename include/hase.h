@@ -46,6 +46,8 @@
  *                                of every agent (only with HASE_EXPORT_STATE)
  *   ep_t     uint32 [n_envs]     steps into the current episode
  *                                (only with HASE_EXPORT_STATE)
+ *   fog      uint64 [fog_words]  env e at fog_off[e]: [U(e)][2][S]
+ *                                (only with HASE_EXPORT_FOG)
  * A_obs(e) counts the agents whose team emits observations (seekers first).
  * Pointers returned by the *_ptr calls stay valid until hase_destroy; their
  * contents are valid once the stream work that wrote them has completed.
@@ -111,6 +113,19 @@ typedef enum hase_status {
                                 /* 2 EXPORT_STATE, 3 SKIP_OBS|EXPORT_CENTRAL,*/
                                 /* 4 3 + EXPORT_STATE, 5 SKIP_OBS|EXPORT_    */
                                 /* STATE, 6 SKIP_OBS (rewards and done only) */
+#define HASE_EXPORT_FOG 256u    /* also write the fog of war [Sec. 3.3, the  */
+                                /* discovery-map layer of Sec. 4, the diff   */
+                                /* sweep of Sec. 5]: a cell is discovered    */
+                                /* once an observing agent of the unit has   */
+                                /* seen it (in its window; visible with      */
+                                /* HASE_OBS_LOS) in the current episode.     */
+                                /* Per env U units -- 1 (all observing       */
+                                /* agents) or, with HASE_FOG_PER_AGENT, one  */
+                                /* per observing agent, seekers first --     */
+                                /* each two planes of S rows (bit x =        */
+                                /* column x): discovered, newly discovered   */
+                                /* in this step.  A reset starts a new map.  */
+#define HASE_FOG_PER_AGENT 512u /* one fog unit per observing agent          */
 #define HASE_POOL_ALLOC 8u      /* buffers from the device's stream-ordered  */
                                 /* pool (allocated on the create stream,     */
                                 /* returned by hase_destroy on the stream of */
@@ -173,6 +188,8 @@ typedef struct hase_layout {
     const uint64_t *unp_off;
     uint64_t central_words;  /* centralized observation words per slot     */
     const uint64_t *central_off; /* env e at central_off[e]: [4][side] words */
+    uint64_t fog_words;      /* fog-of-war words per slot                   */
+    const uint64_t *fog_off; /* env e at fog_off[e]: [U][2][side] words     */
 } hase_layout;
 
 typedef struct hase_handle hase_handle;
@@ -210,6 +227,8 @@ hase_status hase_central_ptr(hase_handle *h, uint64_t **central);
 /* The true-state rings (HASE_EXPORT_STATE; NULL without it): cells
  * [ring_steps][agents] and ep_t [ring_steps][n_envs]. */
 hase_status hase_state_ptr(hase_handle *h, uint16_t **cells, uint32_t **ep_t);
+/* The fog-of-war ring (HASE_EXPORT_FOG; NULL without it). */
+hase_status hase_fog_ptr(hase_handle *h, uint64_t **fog);
 hase_status hase_layout_get(hase_handle *h, hase_layout *out);
 
 /* The same n_steps as one CUDA graph: the first call for a given n_steps

@@ -27,6 +27,9 @@ cudaError_t launch_central_init(const EnvRT* env, uint32_t n_envs, const uint16_
                                 const uint32_t* coff, uint64_t* central, cudaStream_t st);
 cudaError_t launch_state_init(const uint16_t* pos, const EnvState* est, uint32_t agents, uint32_t n_envs,
                               uint16_t* cells, uint32_t* ept, cudaStream_t st);
+cudaError_t launch_fog_init(const EnvRT* env, uint32_t n_envs, const uint16_t* pos, const uint64_t* rows,
+                            const uint32_t* foff, uint32_t per_agent, uint64_t* fog, uint64_t* state,
+                            cudaStream_t st);
 cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
                           uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
                           uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
@@ -51,6 +54,14 @@ struct hase_handle {
     uint32_t* d_coff = nullptr;
     uint16_t* d_cells = nullptr;  // true state rings (HASE_EXPORT_STATE)
     uint32_t* d_ept = nullptr;
+    // fog of war (HASE_EXPORT_FOG): ring, per-env offsets, discovery rows
+    std::vector<uint64_t> fog_off;
+    std::vector<uint32_t> fog_off32;
+    uint64_t fog_words = 0;
+    uint16_t fog_flags = 0;  // group flags kFog | kFogAgent
+    uint64_t* d_fog = nullptr;
+    uint32_t* d_fog_off = nullptr;
+    uint64_t* d_fog_state = nullptr;
     uint64_t agents = 0, obs_words = 0, unp_bytes = 0, rows_words = 0;
     uint32_t smem = 0, threads = 0, kc = 16, emit_warps = 0, steps_per_launch = 0, n_dyn = 1;
     uint32_t smem_budget = kSmemBudget;
@@ -114,7 +125,8 @@ static hase_status cuda_fail(hase_handle* h, cudaError_t e, const char* what) {
 static void free_all(hase_handle* h) {
     void* ptrs[] = {h->d_env, h->d_est,  h->d_pos, h->d_start, h->d_rows, h->d_groups,
                     h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr, h->d_env_list,
-                    h->d_clock, h->d_scratch, h->d_central, h->d_coff, h->d_cells, h->d_ept};
+                    h->d_clock, h->d_scratch, h->d_central, h->d_coff, h->d_cells, h->d_ept,
+                    h->d_fog, h->d_fog_off, h->d_fog_state};
     const bool pool = h->flags & HASE_POOL_ALLOC;
     for (void* p : ptrs)
         if (p) {
@@ -205,7 +217,7 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             if (g.n_slots + En.n_agents > (uint32_t)kMaxGroupSlots) break;
             if (many && g.n_slots + En.n_agents > 32u) break;
             genv.push_back(En);
-            uint16_t flags = 0;
+            const uint16_t flags = h->fog_flags;
             if (!plan_group(genv.data(), (int)genv.size(), (int)h->kc, flags, plan) ||
                 plan.total > h->smem_budget) {
                 genv.pop_back();
@@ -216,8 +228,8 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             ++i;
         }
         if (g.n_envs == 0) return false;  // one env alone exceeds the budget
-        uint16_t flags = 0;
-        plan_group(genv.data(), g.n_envs, (int)h->kc, kUseTable, plan);
+        uint16_t flags = h->fog_flags;
+        plan_group(genv.data(), g.n_envs, (int)h->kc, flags | kUseTable, plan);
         if (plan.total <= h->smem_budget) flags |= kUseTable;
         plan_group(genv.data(), g.n_envs, (int)h->kc, flags, plan);
         g.flags = flags;
@@ -254,10 +266,13 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if ((uint64_t)cfg->env_id_base + cfg->n_envs > 0x100000000ull)
         return fail(nullptr, HASE_EINVAL, "env ids exceed 32 bits");
     if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED | HASE_ASYNC_CREATE | HASE_POOL_ALLOC |
-                       HASE_DESYNC_START | HASE_EXPORT_CENTRAL | HASE_EXPORT_STATE | HASE_SKIP_OBS))
+                       HASE_DESYNC_START | HASE_EXPORT_CENTRAL | HASE_EXPORT_STATE | HASE_SKIP_OBS |
+                       HASE_EXPORT_FOG | HASE_FOG_PER_AGENT))
         return fail(nullptr, HASE_EINVAL, "unknown flags 0x%x", cfg->flags);
     if ((cfg->flags & HASE_SKIP_OBS) && (cfg->flags & HASE_EXPORT_UNPACKED))
         return fail(nullptr, HASE_EINVAL, "HASE_EXPORT_UNPACKED needs the decentralized observation");
+    if ((cfg->flags & HASE_FOG_PER_AGENT) && !(cfg->flags & HASE_EXPORT_FOG))
+        return fail(nullptr, HASE_EINVAL, "HASE_FOG_PER_AGENT needs HASE_EXPORT_FOG");
     if (cfg->chunk_steps != 0 && (cfg->chunk_steps < 1 || cfg->chunk_steps > (uint32_t)kMaxChunk))
         return fail(nullptr, HASE_EINVAL, "chunk_steps outside 1..%d", kMaxChunk);
     if (cfg->emit_warps > 12) return fail(nullptr, HASE_EINVAL, "emit_warps outside 1..12");
@@ -331,7 +346,18 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     h->central_off.assign(h->n_envs + 1, 0);
     for (uint32_t e = 0; e < h->n_envs; ++e) h->central_off[e + 1] = h->central_off[e] + 4ull * h->env[e].side;
     h->central_words = (h->flags & HASE_EXPORT_CENTRAL) ? h->central_off[h->n_envs] : 0;
-    if (h->obs_words > 0xffffffffull || h->agents > 0xffffffffull || h->unp_bytes > 0xffffffffull) {
+    // fog of war: per env [units][2][side] words (offsets all 0 without it)
+    h->fog_off.assign(h->n_envs + 1, 0);
+    if (h->flags & HASE_EXPORT_FOG) {
+        const bool per_agent = (h->flags & HASE_FOG_PER_AGENT) != 0u;
+        h->fog_flags = (uint16_t)(kFog | (per_agent ? kFogAgent : 0u));
+        for (uint32_t e = 0; e < h->n_envs; ++e)
+            h->fog_off[e + 1] = h->fog_off[e] + 2ull * fog_units(h->env[e], per_agent) * h->env[e].side;
+        h->fog_words = h->fog_off[h->n_envs];
+        h->fog_off32.assign(h->fog_off.begin(), h->fog_off.end() - 1);
+    }
+    if (h->obs_words > 0xffffffffull || h->agents > 0xffffffffull || h->unp_bytes > 0xffffffffull ||
+        h->central_words > 0xffffffffull || h->fog_words > 0xffffffffull) {
         delete h;
         return fail(nullptr, HASE_EINVAL, "per-step output slice exceeds 2^32 entries");
     }
@@ -400,6 +426,11 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         HASE_ALLOC(h->d_cells, 2 * R * h->agents);
         HASE_ALLOC(h->d_ept, 4 * R * h->n_envs);
     }
+    if (h->flags & HASE_EXPORT_FOG) {
+        HASE_ALLOC(h->d_fog, 8 * R * h->fog_words);
+        HASE_ALLOC(h->d_fog_off, 4 * h->n_envs);
+        HASE_ALLOC(h->d_fog_state, 4 * h->fog_words);  // half the words of a slot
+    }
     HASE_ALLOC(h->d_err, 4);
     HASE_ALLOC(h->d_thr, 4 * h->n_envs);
     HASE_ALLOC(h->d_clock, 8);
@@ -454,6 +485,13 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         return s;
     if (h->d_ept && (s = finish(cudaMemsetAsync(h->d_ept, 0, 4 * R * h->n_envs, st), "memset")) != HASE_OK)
         return s;
+    if (h->d_fog) {
+        if ((s = finish(cudaMemsetAsync(h->d_fog, 0, 8 * R * h->fog_words, st), "memset")) != HASE_OK) return s;
+        if ((s = finish(cudaMemcpyAsync(h->d_fog_off, h->fog_off32.data(), 4 * h->n_envs, cudaMemcpyHostToDevice,
+                                        st),
+                        "copy fog offsets")) != HASE_OK)
+            return s;
+    }
     const uint32_t key0 = (uint32_t)(h->seed & 0xffffffffu), key1 = (uint32_t)(h->seed >> 32);
     if ((s = finish(launch_generate(h->d_env, h->d_thr, h->n_envs, key0, key1, h->d_pos, h->d_start, h->d_rows,
                                     h->d_err, st), "generate")) != HASE_OK)
@@ -467,6 +505,11 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
                                                     h->d_cells + last * h->agents, h->d_ept + last * h->n_envs,
                                                     st),
                                   "true state")) != HASE_OK)
+        return s;
+    if (h->d_fog && (s = finish(launch_fog_init(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_fog_off,
+                                                (h->flags & HASE_FOG_PER_AGENT) ? 1u : 0u,
+                                                h->d_fog + last * h->fog_words, h->d_fog_state, st),
+                                "fog of war")) != HASE_OK)
         return s;
     if (h->d_central) {
         std::vector<uint32_t> coff(h->n_envs);
@@ -518,6 +561,10 @@ hase_status hase_reset(hase_handle* h, void* stream) {
     if (h->d_cells)
         HASE_CUDA(h, launch_state_init(h->d_pos, h->d_est, (uint32_t)h->agents, h->n_envs,
                                        h->d_cells + last * h->agents, h->d_ept + last * h->n_envs, st));
+    if (h->d_fog)
+        HASE_CUDA(h, launch_fog_init(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_fog_off,
+                                     (h->flags & HASE_FOG_PER_AGENT) ? 1u : 0u, h->d_fog + last * h->fog_words,
+                                     h->d_fog_state, st));
     HASE_CUDA(h, cudaMemsetAsync(h->d_clock, 0, 8, st));
     h->t = 0;
     return HASE_OK;
@@ -548,6 +595,10 @@ static hase_status enqueue_steps(hase_handle* h, uint32_t n_steps, cudaStream_t 
         p.central_words = h->central_words;
         p.st_cells = h->d_cells;
         p.st_ept = h->d_ept;
+        p.fog = h->d_fog;
+        p.fog_off = h->d_fog_off;
+        p.fog_state = h->d_fog_state;
+        p.fog_words = h->fog_words;
         p.obs_words = h->obs_words;
         p.agents = h->agents;
         p.unp_bytes = h->unp_bytes;
@@ -643,6 +694,12 @@ hase_status hase_central_ptr(hase_handle* h, uint64_t** central) {
     return HASE_OK;
 }
 
+hase_status hase_fog_ptr(hase_handle* h, uint64_t** fog) {
+    if (!h || !fog) return fail(h, HASE_EINVAL, "NULL argument");
+    *fog = h->d_fog;
+    return HASE_OK;
+}
+
 hase_status hase_state_ptr(hase_handle* h, uint16_t** cells, uint32_t** ep_t) {
     if (!h || !cells || !ep_t) return fail(h, HASE_EINVAL, "NULL argument");
     *cells = h->d_cells;
@@ -668,6 +725,8 @@ hase_status hase_layout_get(hase_handle* h, hase_layout* out) {
     out->unp_off = h->unp_off.data();
     out->central_words = h->central_words;
     out->central_off = h->central_off.data();
+    out->fog_words = h->fog_words;
+    out->fog_off = h->fog_off.data();
     return HASE_OK;
 }
 
@@ -681,7 +740,7 @@ static const uint64_t kBlobMagic = 0x3130455341484742ull;  // "BGHASE01"
 
 hase_status hase_get_state(hase_handle* h, void* buf, size_t* size, void* stream) {
     if (!h || !size) return fail(h, HASE_EINVAL, "NULL argument");
-    const size_t need = 4 * 8 + 2 * h->agents + sizeof(EnvState) * h->n_envs;
+    const size_t need = 4 * 8 + 2 * h->agents + sizeof(EnvState) * h->n_envs + 4 * h->fog_words;
     if (!buf) {
         *size = need;
         return HASE_OK;
@@ -697,6 +756,9 @@ hase_status hase_get_state(hase_handle* h, void* buf, size_t* size, void* stream
     HASE_CUDA(h, cudaMemcpyAsync(p, h->d_pos, 2 * h->agents, cudaMemcpyDeviceToHost, st));
     HASE_CUDA(h, cudaMemcpyAsync(p + 2 * h->agents, h->d_est, sizeof(EnvState) * h->n_envs,
                                  cudaMemcpyDeviceToHost, st));
+    if (h->d_fog_state)
+        HASE_CUDA(h, cudaMemcpyAsync(p + 2 * h->agents + sizeof(EnvState) * h->n_envs, h->d_fog_state,
+                                     4 * h->fog_words, cudaMemcpyDeviceToHost, st));
     HASE_CUDA(h, cudaStreamSynchronize(st));
     *size = need;
     return HASE_OK;
@@ -704,7 +766,7 @@ hase_status hase_get_state(hase_handle* h, void* buf, size_t* size, void* stream
 
 hase_status hase_set_state(hase_handle* h, const void* buf, size_t size, void* stream) {
     if (!h || !buf) return fail(h, HASE_EINVAL, "NULL argument");
-    const size_t need = 4 * 8 + 2 * h->agents + sizeof(EnvState) * h->n_envs;
+    const size_t need = 4 * 8 + 2 * h->agents + sizeof(EnvState) * h->n_envs + 4 * h->fog_words;
     if (size != need) return fail(h, HASE_EINVAL, "state blob has %zu bytes, expected %zu", size, need);
     const uint64_t* hdr = (const uint64_t*)buf;
     if (hdr[0] != kBlobMagic || hdr[1] != h->n_envs || hdr[2] != h->agents)
@@ -721,9 +783,22 @@ hase_status hase_set_state(hase_handle* h, const void* buf, size_t size, void* s
                 return fail(h, HASE_EINVAL, "state blob: agent %u of env %u off the grid", a, e);
         }
     }
+    // discovery rows: no bits outside the env's columns
+    const uint8_t* pf = p + 2 * h->agents + sizeof(EnvState) * h->n_envs;
+    for (uint32_t e = 0; h->d_fog_state && e < h->n_envs; ++e) {
+        const uint32_t S = h->env[e].side;
+        const uint64_t smask = S == 64 ? ~0ull : ((1ull << S) - 1ull);
+        for (uint64_t i = h->fog_off[e] / 2; i < h->fog_off[e + 1] / 2; ++i) {
+            uint64_t v;
+            memcpy(&v, pf + 8 * i, 8);
+            if (v & ~smask) return fail(h, HASE_EINVAL, "state blob: fog row of env %u outside the grid", e);
+        }
+    }
     HASE_CUDA(h, cudaMemcpyAsync(h->d_pos, p, 2 * h->agents, cudaMemcpyHostToDevice, st));
     HASE_CUDA(h, cudaMemcpyAsync(h->d_est, p + 2 * h->agents, sizeof(EnvState) * h->n_envs,
                                  cudaMemcpyHostToDevice, st));
+    if (h->d_fog_state)
+        HASE_CUDA(h, cudaMemcpyAsync(h->d_fog_state, pf, 4 * h->fog_words, cudaMemcpyHostToDevice, st));
     const uint64_t tt = hdr[3];
     HASE_CUDA(h, cudaMemcpyAsync(h->d_clock, &tt, 8, cudaMemcpyHostToDevice, st));
     HASE_CUDA(h, cudaStreamSynchronize(st));

@@ -57,6 +57,8 @@ struct EnvState {
 
 // Group flags.
 constexpr uint16_t kUseTable = 1;   // obstacle plane from per-cell window tables
+constexpr uint16_t kFog = 2;        // fog-of-war maps (one unit per env)
+constexpr uint16_t kFogAgent = 4;   // with kFog: one unit per observing agent
 
 // All envs of a group share the radii, the emitting teams, the row width and
 // the agent and seeker counts, so one code path serves the whole CTA.
@@ -98,13 +100,14 @@ struct GroupPlan {
     uint32_t rows_off[kMaxGroupEnvs];    // uint64 units (padded obstacle rows)
     uint32_t cell_off[kMaxGroupEnvs];    // cells (2^sh * side per env): claim word + state byte
     uint32_t tbl_off[kMaxGroupEnvs][2];  // uint64 units per team, ~0u = none
+    uint32_t fog_off[kMaxGroupEnvs + 1]; // fog-of-war rows (uint64 units; [units][side] per env)
     uint8_t first_slot[kMaxGroupEnvs];
     uint8_t dyn_first[kMaxDyn + 1];      // slot range of every dynamics warp
     uint32_t n_dyn;
     uint32_t n_envs;
     uint32_t n_slots;
     uint32_t act_words;                  // uint32 words per action buffer
-    uint32_t act, traj, rows, claim, tbl, state, total;  // byte offsets
+    uint32_t act, traj, rows, claim, tbl, state, fog, total;  // byte offsets
     uint16_t flags;
 };
 
@@ -125,11 +128,18 @@ __host__ __device__ inline int family_of(const EnvRT& E) {
     return (E.wpp == 2 ? 5 : 1) + ((int)E.n_agents - 1) / 4;
 }
 
+// Fog-of-war units of an env: all observing agents together, or each
+// observing agent (seekers first).
+__host__ __device__ inline uint32_t fog_units(const EnvRT& E, bool per_agent) {
+    if (!per_agent) return 1u;
+    return (team_sees(E, 0) ? E.n_seekers : 0u) + (team_sees(E, 1) ? E.n_agents - E.n_seekers : 0u);
+}
+
 // envs: the group's env constants in slot order.  Returns false when the
 // group does not fit the dynamics warps.
 __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uint16_t flags,
                                            GroupPlan& G) {
-    uint32_t ro = 0, co = 0, to = 0, slot = 0;
+    uint32_t ro = 0, co = 0, to = 0, fo = 0, slot = 0;
     int dyn = 0;
     uint32_t dyn_slots = 0;
     G.dyn_first[0] = 0;
@@ -148,6 +158,8 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
         ro += (uint32_t)(E.side + 2 * kPad) * E.rw;
         G.cell_off[i] = co;
         co += (1u << cell_shift(E)) * E.side;
+        G.fog_off[i] = fo;
+        if (flags & kFog) fo += fog_units(E, (flags & kFogAgent) != 0) * E.side;
         for (int t = 0; t < 2; ++t) {
             G.tbl_off[i][t] = ~0u;
             if (!(flags & kUseTable) || !team_emits(E, t)) continue;
@@ -159,6 +171,7 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
             to += (uint32_t)E.side * E.side * table_words(E, team_radius(E, t));
         }
     }
+    G.fog_off[n] = fo;
     G.n_dyn = (uint32_t)dyn + 1;
     G.n_envs = (uint32_t)n;
     G.n_slots = slot;
@@ -171,7 +184,8 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
     G.claim = G.rows + ro * 8;                           // uint32 per cell
     G.tbl = align_up(G.claim + co * 4, 16);
     G.state = G.tbl + to * 8;                            // uint8 per cell
-    G.total = align_up(G.state + co, 16);
+    G.fog = align_up(G.state + co, 16);                  // uint64 per fog row
+    G.total = align_up(G.fog + fo * 8, 16);
     G.flags = flags;
     return true;
 }
@@ -217,6 +231,10 @@ struct StepParams {
     uint8_t* unp;        // ring [ring][unp_bytes] or null
     uint64_t* central;   // ring [ring][central_words] or null (centralized observation)
     const uint32_t* central_off;  // per env: first word of its centralized observation
+    uint64_t* fog;       // ring [ring][fog_words] or null (fog of war)
+    const uint32_t* fog_off;  // per env: first word of its fog units in a slot
+    uint64_t* fog_state; // per env at fog_off / 2: the discovery rows after the last step
+    uint64_t fog_words;
     uint16_t* st_cells;  // ring [ring][agents] or null (true state: cells x | y << 6)
     uint32_t* st_ept;    // ring [ring][n_envs] or null (true state: episode clocks)
     uint64_t central_words;

@@ -4,8 +4,8 @@
 //   gen_kernel      a0: start cells and Bernoulli obstacle rows (Sec. 3.2,
 //                   Sec. 4.2 pristine template), one warp per env
 //   observe_kernel  the step -1 observation after create / reset (and
-//                   central_init_kernel, state_init_kernel: its centralized
-//                   observation and true state)
+//                   central_init_kernel, state_init_kernel, fog_init_kernel:
+//                   its centralized observation, true state and fog of war)
 //   digest kernels  the run summary of hase_digest / hase_digest_noalloc
 //   advance_kernel  the device step counter
 // and the host launchers; the step kernel itself is in hase_step.cuh.
@@ -169,6 +169,41 @@ cudaError_t launch_state_init(const uint16_t* pos, const EnvState* est, uint32_t
     const uint32_t n = agents > n_envs ? agents : n_envs;
     if (n == 0) return cudaSuccess;
     state_init_kernel<<<(n + 255) / 256, 256, 0, st>>>(pos, est, agents, n_envs, cells, ept);
+    return cudaGetLastError();
+}
+
+// The fog of war after create / reset: the first observation of an episode
+// starts every map (discovered = newly discovered = seen), one thread per env.
+__global__ void fog_init_kernel(const EnvRT* __restrict__ env, uint32_t n_envs, const uint16_t* __restrict__ pos,
+                                const uint64_t* __restrict__ rows, const uint32_t* __restrict__ foff,
+                                uint32_t per_agent, uint64_t* __restrict__ fog, uint64_t* __restrict__ state) {
+    const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_envs) return;
+    const EnvRT E = env[e];
+    const uint32_t S = E.side, units = fog_units(E, per_agent != 0u);
+    const int ns = E.n_seekers;
+    const uint16_t* p = pos + E.agent_off;
+    for (uint32_t j = 0; j < units; ++j) {
+        const int a0 = per_agent ? (team_sees(E, 0) ? (int)j : ns + (int)j) : 0;
+        const int a1 = per_agent ? a0 + 1 : (int)E.n_agents;
+        for (uint32_t y = 0; y < S; ++y) {
+            uint64_t seen = 0;
+            for (int a = a0; a < a1; ++a) {
+                const int team = a < ns ? 0 : 1;
+                if (team_sees(E, team)) seen |= agent_seen_row(E, rows + E.rows_off, p[a], 6u, team, (int)y);
+            }
+            fog[foff[e] + j * 2u * S + y] = seen;
+            fog[foff[e] + j * 2u * S + S + y] = seen;
+            state[foff[e] / 2u + j * S + y] = seen;
+        }
+    }
+}
+
+cudaError_t launch_fog_init(const EnvRT* env, uint32_t n_envs, const uint16_t* pos, const uint64_t* rows,
+                            const uint32_t* foff, uint32_t per_agent, uint64_t* fog, uint64_t* state,
+                            cudaStream_t st) {
+    if (n_envs == 0) return cudaSuccess;
+    fog_init_kernel<<<(n_envs + 63) / 64, 64, 0, st>>>(env, n_envs, pos, rows, foff, per_agent, fog, state);
     return cudaGetLastError();
 }
 

@@ -111,6 +111,33 @@ __device__ inline void window_visibility(uint64_t lo, uint64_t hi, int r, uint64
 // 1 seen obstacles, 2 seen seekers, 3 seen hiders; bit x of row y is cell
 // (x, y).  src holds the agents' cells packed x | y << sh; rows are the env's
 // padded obstacle rows.
+// Row dy (-R..R) of a window's visibility mask (vl, vh: window bits k =
+// (dy + R)(2R + 1) + (dx + R)), as 2R + 1 bits.
+__device__ __forceinline__ uint64_t window_row(uint64_t vl, uint64_t vh, int R, int dy) {
+    const int D = 2 * R + 1, off = (dy + R) * D;
+    return off >= 64 ? vh >> (off - 64) : (vl >> off) | (off + D > 64 ? vh << (64 - off) : 0ull);
+}
+
+// Row y of the cells agent (cell v = x | y << sh) of `team` sees: its window
+// and, with line of sight, only the visible part; bit x = column x.
+__device__ inline uint64_t agent_seen_row(const EnvRT& E, const uint64_t* rows, uint32_t v, uint32_t sh, int team,
+                                          int y) {
+    const int R = team_radius(E, team), D = 2 * R + 1;
+    const int xa = (int)(v & ((1u << sh) - 1u)), ya = (int)(v >> sh);
+    const int dy = y - ya;
+    if (dy < -R || dy > R) return 0ull;
+    uint64_t wrow = (1ull << D) - 1ull;
+    if (line_of_sight(E)) {
+        uint64_t lo, hi, vl, vh;
+        obstacle_plane(rows, E.rw, xa, ya, R, lo, hi);
+        window_visibility(lo, hi, R, vl, vh);
+        wrow &= window_row(vl, vh, R, dy);
+    }
+    const int x0 = xa - R;
+    const uint64_t smask = E.side == 64 ? ~0ull : ((1ull << E.side) - 1ull);
+    return (x0 >= 0 ? (wrow << x0) : (wrow >> (-x0))) & smask;
+}
+
 __device__ inline void central_env(const EnvRT& E, const uint64_t* rows, const uint16_t* src, uint32_t sh,
                                    uint64_t* out) {
     const int S = E.side, A = E.n_agents, ns = E.n_seekers, rw = E.rw;
@@ -147,12 +174,7 @@ __device__ inline void central_env(const EnvRT& E, const uint64_t* rows, const u
             const int dy = y - ya;
             if (dy < -R || dy > R) continue;
             uint64_t wrow = (1ull << D) - 1ull;
-            if (los) {  // row dy of the window's visible cells
-                const int off = (dy + R) * D;
-                const uint64_t bits = off >= 64 ? vh[a] >> (off - 64)
-                                                : (vl[a] >> off) | (off + D > 64 ? vh[a] << (64 - off) : 0ull);
-                wrow &= bits;
-            }
+            if (los) wrow &= window_row(vl[a], vh[a], R, dy);  // row dy of the window's visible cells
             const int x0 = xa - R;
             seen |= x0 >= 0 ? (wrow << x0) : (wrow >> (-x0));
         }
@@ -204,6 +226,7 @@ struct CtaShared {
     uint32_t gidx[kMaxGroupEnvs];  // handle env index (done byte, counters)
     uint32_t coff[kMaxGroupEnvs];  // first word of the env's centralized observation
     uint32_t ept0[kMaxGroupEnvs];  // episode clock before the launch's first step
+    uint32_t foff[kMaxGroupEnvs];  // first word of the env's fog units in a slot
     GroupPlan plan;
     SlotRec slot[kMaxGroupSlots];
     uint16_t p0[kMaxGroupSlots];  // pristine start cells (CTA packing)
@@ -849,6 +872,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             H.gidx[i] = g;
             H.coff[i] = P.central ? P.central_off[g] : 0u;
             H.ept0[i] = P.st_ept ? P.est[g].ep_t : 0u;
+            H.foff[i] = P.fog ? P.fog_off[g] : 0u;
             uint32_t urel = E.unp_off;
             for (int a = 0; a < E.n_agents; ++a) {
                 const int t = a < E.n_seekers ? 0 : 1;
@@ -876,8 +900,21 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
     uint32_t* s_claim = (uint32_t*)(sm + L.claim);   // per cell
     uint8_t* s_state = sm + L.state;                 // per cell
     uint64_t* s_tbl = (uint64_t*)(sm + L.tbl);
+    uint64_t* s_fog = (uint64_t*)(sm + L.fog);     // per fog row: discovered cells
     const uint32_t act_bytes = L.act_words * 4;
+    const uint32_t fog_rows = L.fog_off[ne];
+    // env of fog row u (rows are grouped by env)
+    auto fog_env_of = [&](uint32_t u) {
+        int e = 0;
+        while (L.fog_off[e + 1] <= u) ++e;
+        return e;
+    };
 
+    // the discovery rows after the previous launch
+    for (uint32_t u = tid; u < fog_rows; u += nthreads) {
+        const int e = fog_env_of(u);
+        s_fog[u] = P.fog_state[H.foff[e] / 2u + (u - L.fog_off[e])];
+    }
     // stage the pristine template: padded rows and start cells
     for (int i = 0; i < ne; ++i) {
         const EnvRT& E = H.env[i];
@@ -1155,10 +1192,50 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                     }
                 }
             }
+            // Fog of war: one thread per fog row (env, unit, row y) scans the
+            // chunk's steps in order; an episode's first observation (a done
+            // step: the reset state) starts the row afresh.
+            const bool per_agent = (L.flags & kFogAgent) != 0;
+            for (uint32_t u = (uint32_t)worker; u < fog_rows; u += (uint32_t)n_workers) {
+                const int e = fog_env_of(u);
+                const EnvRT& E = H.env[e];
+                const uint32_t S = E.side, sh = cell_shift(E);
+                const uint32_t rel = u - L.fog_off[e], j = rel / S, y = rel - j * S;
+                const int ns = E.n_seekers;
+                const int a0 = per_agent ? (team_sees(E, 0) ? (int)j : ns + (int)j) : 0;
+                const int a1 = per_agent ? a0 + 1 : (int)E.n_agents;
+                const int first = L.first_slot[e];
+                const uint64_t* rows_e = C.rows + L.rows_off[e];
+                uint64_t* out = P.fog + H.foff[e] + j * 2u * S + y;
+                uint64_t disc = s_fog[u];
+                for (uint32_t k = 0; k < C.len; ++k) {
+                    const uint16_t* Tk = C.T + k * nsl + first;
+                    const bool done = (Tk[0] & kDoneBit) != 0u;
+                    const uint16_t* src = done ? H.p0 + first : Tk;
+                    uint64_t seen = 0;
+                    for (int a = a0; a < a1; ++a) {
+                        const int team = a < ns ? 0 : 1;
+                        if (team_sees(E, team)) seen |= agent_seen_row(E, rows_e, src[a] & 0x0fffu, sh, team, (int)y);
+                    }
+                    const uint64_t prev = done ? 0ull : disc;
+                    disc = prev | seen;
+                    uint32_t sl = C.base_slot + k;
+                    if (sl >= P.ring) sl -= P.ring;
+                    uint64_t* o = out + (uint64_t)sl * P.fog_words;
+                    o[0] = disc;
+                    o[S] = seen & ~prev;
+                }
+                s_fog[u] = disc;
+            }
         }
         // a1 for chunk c + 1
         if (c + 1 < n_chunks) draw_actions(c + 1, worker, n_workers);
         __syncthreads();
+    }
+    // the discovery rows for the next launch
+    for (uint32_t u = (uint32_t)worker; u < fog_rows; u += (uint32_t)n_workers) {
+        const int e = fog_env_of(u);
+        P.fog_state[H.foff[e] / 2u + (u - L.fog_off[e])] = s_fog[u];
     }
 }
 

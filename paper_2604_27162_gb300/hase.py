@@ -28,6 +28,8 @@ HASE_DESYNC_START = 16
 HASE_EXPORT_CENTRAL = 32
 HASE_EXPORT_STATE = 64
 HASE_SKIP_OBS = 128
+HASE_EXPORT_FOG = 256
+HASE_FOG_PER_AGENT = 512
 HASE_OBS_LOS = 4
 HASE_OBS_SEEKERS = 1
 HASE_OBS_HIDERS = 2
@@ -38,7 +40,7 @@ STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA
 EXPORTS = [
     "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_digest", "hase_digest_noalloc",
     "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
-    "hase_actions_ptr", "hase_central_ptr", "hase_state_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
+    "hase_actions_ptr", "hase_central_ptr", "hase_state_ptr", "hase_fog_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
     "hase_get_world", "hase_sync", "hase_launch_info", "hase_destroy", "hase_last_error",
     "hase_request_bytes", "hase_serve",
 ]
@@ -135,6 +137,8 @@ class hase_layout(C.Structure):
         ("unp_off", C.POINTER(C.c_uint64)),
         ("central_words", C.c_uint64),
         ("central_off", C.POINTER(C.c_uint64)),
+        ("fog_words", C.c_uint64),
+        ("fog_off", C.POINTER(C.c_uint64)),
     ]
 
 
@@ -167,6 +171,7 @@ def load(path=LIB_PATH):
     L.hase_actions_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_central_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_state_ptr.argtypes = [H, C.POINTER(P), C.POINTER(P)]
+    L.hase_fog_ptr.argtypes = [H, C.POINTER(P)]
     L.hase_layout_get.argtypes = [H, C.POINTER(hase_layout)]
     L.hase_step_count.argtypes = [H, C.POINTER(u64)]
     L.hase_get_state.argtypes = [H, P, C.POINTER(C.c_size_t), P]
@@ -311,6 +316,12 @@ def hase_central_ptr(h):
     return a.value
 
 
+def hase_fog_ptr(h):
+    a = C.c_void_p()
+    _check(load().hase_fog_ptr(h, C.byref(a)), h)
+    return a.value
+
+
 def hase_state_ptr(h):
     """(cells, ep_t) device pointers of the true-state rings, or (None, None)."""
     a, b = C.c_void_p(), C.c_void_p()
@@ -333,6 +344,8 @@ def hase_layout_get(h):
         "unp_off": np.ctypeslib.as_array(lay.unp_off, shape=(n,)).copy(),
         "central_words": lay.central_words,
         "central_off": np.ctypeslib.as_array(lay.central_off, shape=(n,)).copy(),
+        "fog_words": lay.fog_words,
+        "fog_off": np.ctypeslib.as_array(lay.fog_off, shape=(n,)).copy(),
     }
 
 
@@ -428,6 +441,8 @@ class Engine:
         cells, ept = hase_state_ptr(self.h)
         self.cells = device_view(cells, (ring_steps, L["agents"]), "i16", self) if cells else None
         self.ep_t = device_view(ept, (ring_steps, n_envs), "i32", self) if ept else None
+        fog = hase_fog_ptr(self.h)
+        self.fog = device_view(fog, (ring_steps, L["fog_words"]), "i64", self) if fog else None
 
     def slot(self, t):
         """Ring slot of global step t (t = -1: the observation after create/reset)."""

@@ -23,6 +23,8 @@ def engine_outputs(eng):
         out["unpacked"] = eng.unpacked.cpu().numpy()
     if eng.central is not None:
         out["central"] = eng.central.cpu().numpy().view(np.uint64)
+    if eng.fog is not None:
+        out["fog"] = eng.fog.cpu().numpy().view(np.uint64)
     if eng.cells is not None:
         out["cells"] = eng.cells.cpu().numpy().view(np.uint16)
         out["ep_t"] = eng.ep_t.cpu().numpy().view(np.uint32)
@@ -50,8 +52,9 @@ def compare_run(n_envs, seed, descs, n_steps, ring=None, flags=hase.HASE_EXPORT_
         assert got["obs"].shape == (ring, 0), got["obs"].shape
         del got["obs"]
     unpacked = bool(flags & hase.HASE_EXPORT_UNPACKED)
+    fog = 0 if not flags & hase.HASE_EXPORT_FOG else (2 if flags & hase.HASE_FOG_PER_AGENT else 1)
     w = oracle.World(n_envs, seed, descs, env_id_base=env_id_base,
-                     desync=bool(flags & hase.HASE_DESYNC_START))
+                     desync=bool(flags & hase.HASE_DESYNC_START), fog=fog)
     if ring > n_steps:
         init = w.observe(unpacked=unpacked)
         o0 = init[0] if unpacked else init
@@ -61,6 +64,8 @@ def compare_run(n_envs, seed, descs, n_steps, ring=None, flags=hase.HASE_EXPORT_
         assert (got["reward"][ring - 1] == 0).all() and (got["done"][ring - 1] == 0).all()
         if "central" in got:
             assert (got["central"][ring - 1] == w.central()).all(), "initial centralized observation"
+        if "fog" in got:
+            assert (got["fog"][ring - 1] == w.fog()).all(), "initial fog of war"
         if "cells" in got:
             cells, ep_t = w.true_state()
             assert (got["cells"][ring - 1] == cells).all(), "initial true state (cells)"
@@ -71,10 +76,12 @@ def compare_run(n_envs, seed, descs, n_steps, ring=None, flags=hase.HASE_EXPORT_
             o["central"] = w.central()
         if "cells" in got:
             o["cells"], o["ep_t"] = w.true_state()
+        if "fog" in got:
+            o["fog"] = w.fog()
         if t < n_steps - ring:
             continue
         s = t % ring
-        for k in ("obs", "reward", "done", "action", "unpacked", "central", "cells", "ep_t"):
+        for k in ("obs", "reward", "done", "action", "unpacked", "central", "cells", "ep_t", "fog"):
             if k in got and k in o:
                 if not (got[k][s] == o[k]).all():
                     bad = np.flatnonzero(got[k][s] != o[k])[:8]

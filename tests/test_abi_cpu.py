@@ -38,7 +38,7 @@ def test_binding_struct_sizes_match_header():
 
     assert ctypes.sizeof(hase.hase_env_desc) == 32
     assert ctypes.sizeof(hase.hase_config) == 56
-    assert ctypes.sizeof(hase.hase_layout) == 72
+    assert ctypes.sizeof(hase.hase_layout) == 88
     assert ctypes.sizeof(hase.hase_digest_out) == 32
     assert ctypes.sizeof(hase.hase_request) == 56
     assert ctypes.sizeof(hase.hase_serve_config) == 24

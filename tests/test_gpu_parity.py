@@ -170,6 +170,52 @@ def test_true_state_uneven_desynchronised_and_reset():
     eng.close()
 
 
+@pytest.mark.parametrize("per_agent", [False, True], ids=["global", "per-agent"])
+@pytest.mark.parametrize("desc", [
+    W.env_desc(32, 10, 5, 3, 2, 40, "0.2"),            # one-thread emission family
+    W.env_desc(24, 7, 4, 4, 4, 31, "0.25"),            # radius 4
+    W.env_desc(16, 6, 2, 3, 1, 30, "0.3", 2),          # lane-per-agent, hiders observe
+    W.env_desc(16, 8, 4, 3, 3, 25, "0.25", 3 | 4),     # line of sight
+    W.env_desc(64, 5, 3, 2, 4, 20, "0.15"),            # 64 columns
+    W.env_desc(9, 4, 2, 2, 2, 33, "0.2", 0),           # nobody observes
+], ids=["fast", "r4", "lane-hiders", "los", "side64", "none"])
+def test_fog_of_war_matches_oracle(desc, per_agent):
+    flags = hase.HASE_EXPORT_FOG | (hase.HASE_FOG_PER_AGENT if per_agent else 0)
+    compare_run(20, 41, [desc], 80, flags=flags, launches=[13, 64, 3], chunk_steps=16)
+
+
+def test_fog_of_war_uneven_graph_desync_and_reset():
+    descs = W.uneven_descs(40, 14)
+    flags = hase.HASE_EXPORT_FOG | hase.HASE_DESYNC_START | hase.HASE_EXPORT_CENTRAL
+    compare_run(40, 9, descs, 70, flags=flags, launches=[("graph", 30), 40])
+    compare_run(40, 9, descs, 70, flags=flags | hase.HASE_FOG_PER_AGENT | hase.HASE_SKIP_OBS, ring=23,
+                launches=[35, ("graph", 35)])
+    eng = hase.Engine(40, 9, descs, 64, flags | hase.HASE_FOG_PER_AGENT)
+    eng.step(50)
+    eng.reset()
+    fog = engine_outputs(eng)["fog"]
+    assert (fog[63] == oracle.World(40, 9, descs, desync=True, fog=2).fog()).all()
+    eng.close()
+
+
+def test_fog_of_war_checkpoint_resume():
+    descs = [W.env_desc(16, 6, 3, 3, 2, 45, "0.2")]
+    flags = hase.HASE_EXPORT_FOG
+    a = hase.Engine(12, 3, descs, 100, flags)
+    a.step(30)
+    blob = hase.hase_get_state(a.h)
+    a.step(30)
+    want = engine_outputs(a)["fog"][30:60]
+    b = hase.Engine(12, 3, descs, 100, flags)
+    b.step(7)  # another history, then the checkpoint
+    hase.hase_set_state(b.h, blob)
+    b.step(30)
+    got = engine_outputs(b)["fog"][30:60]
+    assert (got == want).all()
+    a.close()
+    b.close()
+
+
 def test_ring_wraparound_and_split_launches():
     c = W.ten1k()
     compare_run(64, c["seed"], c["descs"], 300, ring=7, launches=[1, 2, 97, 200])
@@ -253,7 +299,9 @@ def test_invalid_configs_rejected():
         hase.Engine(4, 0, [good], 2, hase.HASE_SKIP_OBS | hase.HASE_EXPORT_UNPACKED)
     assert ei.value.status == hase.HASE_EINVAL
     with pytest.raises(hase.HaseError):
-        hase.Engine(4, 0, [good], 2, 1 << 8)  # unknown flag
+        hase.Engine(4, 0, [good], 2, 1 << 10)  # unknown flag
+    with pytest.raises(hase.HaseError):  # per-agent maps without the fog export
+        hase.Engine(4, 0, [good], 2, hase.HASE_FOG_PER_AGENT)
 
 
 # ---------------------------------------------------------------------------
