@@ -29,16 +29,51 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2604_27162_gb300 import hase as H  # noqa: E402  (constants only; the library loads later)
 from paper_2604_27162_gb300 import workloads as W  # noqa: E402
 
 # Rollout length of one benchmark step per workload (the workload's run).
 RUN_STEPS = {"plain16": 1000, "single1k": 10000, "ten1k": 10000, "uneven64k": 1000, "served": 0}
 
+# Optional parts of the step, measured one at a time on a workload:
+# name -> (engine flags, obs_teams bits added to every env).  "default" is
+# observability mode 1 of Section 3.3; state / central / central-state /
+# state-only / void are its modes 2-6; los, desync and fog the other
+# optional layers.
+MODES = {
+    "default": (0, 0),
+    "los": (0, H.HASE_OBS_LOS),
+    "desync": (H.HASE_DESYNC_START, 0),
+    "state": (H.HASE_EXPORT_STATE, 0),
+    "central": (H.HASE_SKIP_OBS | H.HASE_EXPORT_CENTRAL, 0),
+    "central-state": (H.HASE_SKIP_OBS | H.HASE_EXPORT_CENTRAL | H.HASE_EXPORT_STATE, 0),
+    "state-only": (H.HASE_SKIP_OBS | H.HASE_EXPORT_STATE, 0),
+    "void": (H.HASE_SKIP_OBS, 0),
+    "fog": (H.HASE_EXPORT_FOG, 0),
+    "fog-agent": (H.HASE_EXPORT_FOG | H.HASE_FOG_PER_AGENT, 0),
+}
 
-def algorithmic_bytes_per_env_step(descs, n_envs, unpacked):
+
+def apply_mode(c, mode):
+    """The workload with the mode's obs_teams bits, and the mode's flags."""
+    flags, teams = MODES[mode]
+    if teams:
+        c = dict(c, descs=[dict(d, obs_teams=d["obs_teams"] | teams) for d in c["descs"]])
+    if c["unpacked"] and not flags & H.HASE_SKIP_OBS:
+        flags |= H.HASE_EXPORT_UNPACKED
+    return c, flags
+
+
+def oracle_fog(flags):
+    return 0 if not flags & H.HASE_EXPORT_FOG else (2 if flags & H.HASE_FOG_PER_AGENT else 1)
+
+
+def algorithmic_bytes_per_env_step(descs, n_envs, unpacked, flags=0):
     """Bytes the method must deliver per env-step (obs + reward + done, and
-    the unpacked export when requested); padding bits are counted inside the
-    obs words, the CTA-resident state is not (it is read once per launch)."""
+    the exports the flags ask for: unpacked obs, centralized observation,
+    true state, fog of war); padding bits are counted inside the obs words,
+    the CTA-resident state is not (it is read once per launch)."""
+    skip = bool(flags & H.HASE_SKIP_OBS)
     total = 0
     for e in range(n_envs):
         d = descs[0 if len(descs) == 1 else e]
@@ -54,8 +89,29 @@ def algorithmic_bytes_per_env_step(descs, n_envs, unpacked):
             wmax = max(wmax, (D * D + 63) // 64)
             n_obs += 1
             unp += 3 * D * D
-        total += n_obs * 3 * wmax * 8 + d["n_agents"] * 4 + 1 + (unp if unpacked else 0)
+        S, A = d["side"], d["n_agents"]
+        total += 0 if skip else n_obs * 3 * wmax * 8
+        total += A * 4 + 1 + (unp if unpacked and not skip else 0)
+        if flags & H.HASE_EXPORT_CENTRAL:
+            total += 4 * S * 8
+        if flags & H.HASE_EXPORT_STATE:
+            total += 2 * A + 4
+        if flags & H.HASE_EXPORT_FOG:
+            units = n_obs if flags & H.HASE_FOG_PER_AGENT else 1
+            total += units * 2 * S * 8
     return total / n_envs
+
+
+def oracle_step(w, flags, unpacked):
+    """One oracle step with the mode's outputs (the fog maps are updated by
+    the step itself; ho_fog packs them)."""
+    w.step(unpacked=unpacked and not flags & H.HASE_SKIP_OBS, observe=not flags & H.HASE_SKIP_OBS)
+    if flags & H.HASE_EXPORT_CENTRAL:
+        w.central()
+    if flags & H.HASE_EXPORT_STATE:
+        w.true_state()
+    if flags & H.HASE_EXPORT_FOG:
+        w.fog()
 
 
 def measured_traffic(workload_name):
@@ -234,10 +290,9 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     hase.load()
-    c = workload(args.workload)
+    c, flags = apply_mode(workload(args.workload), args.mode)
     n_envs = c["n_envs"]
     run = args.run_steps or RUN_STEPS[args.workload]
-    flags = hase.HASE_EXPORT_UNPACKED if c["unpacked"] else 0
     # weak scaling: rank r steps envs [r*E, (r+1)*E) of the global batch
     stream = torch.cuda.current_stream()
     form = args.form or ("batched" if args.workload == "uneven64k" else "plain")
@@ -271,11 +326,11 @@ def run_gpu(args):
     ms = S.max_over_ranks(ms, device="cuda")
     agents = sum(c["descs"][0 if len(c["descs"]) == 1 else e]["n_agents"] for e in range(n_envs))
     value = S.weak_throughput(n_envs * run * args.steps, world, ms / 1e3)
-    bpe = algorithmic_bytes_per_env_step(c["descs"], n_envs, c["unpacked"])
+    bpe = algorithmic_bytes_per_env_step(c["descs"], n_envs, c["unpacked"], flags)
     per_rank_bytes = bpe * n_envs * run * args.steps
     achieved = per_rank_bytes / (ms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    tpe = measured_traffic(args.workload)
+    tpe = measured_traffic(args.workload) if args.mode == "default" else None
     traffic = tpe * n_envs * run if tpe is not None else None  # bytes per launch
 
     # end to end through the public API: every step's results copied to
@@ -310,6 +365,8 @@ def run_gpu(args):
             "data": "synthetic (seeded Bernoulli maps, Philox actions)",
             "config": {
                 "workload": args.workload,
+                "mode": args.mode,
+                "flags": flags,
                 "n_envs_per_gpu": n_envs,
                 "env_steps_per_bench_step": run,
                 "descs": c["descs"] if len(c["descs"]) == 1 else "per-env table (%d)" % n_envs,
@@ -336,25 +393,31 @@ def run_gpu(args):
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clk,
             "e2e": e2e,
-            "cpu_baseline": cpu_baseline(c, args) if world == 1 and not args.no_cpu else None,
+            "cpu_baseline": cpu_baseline(c, args, flags) if world == 1 and not args.no_cpu else None,
         }
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
 
 
+def engine_exports(eng):
+    """(name, device ring view) of every output the handle writes."""
+    out = [("obs", eng.obs), ("reward", eng.reward), ("done", eng.done)]
+    for k in ("unpacked", "central", "cells", "ep_t", "fog"):
+        v = getattr(eng, k)
+        if v is not None:
+            out.append((k, v))
+    return [(k, v) for k, v in out if v.shape[1] > 0]
+
+
 def run_e2e(eng, c, run, stream, args):
     import torch
 
     n_steps = run * max(1, min(args.steps, 3))
-    L = eng.layout
-    per_step = L["obs_words"] * 8 + L["agents"] * 4 + eng.n_envs + (L["unp_bytes"] if eng.unpacked is not None else 0)
+    ex = engine_exports(eng)
+    per_step = sum(v.shape[1] * v.element_size() for _, v in ex)
     chunk = max(1, min(1000, run, (1 << 30) // per_step))  # pinned staging of at most 1 GiB
-    h_obs = torch.empty((chunk, L["obs_words"]), dtype=torch.int64, pin_memory=True)
-    h_rew = torch.empty((chunk, L["agents"]), dtype=torch.int32, pin_memory=True)
-    h_done = torch.empty((chunk, eng.n_envs), dtype=torch.uint8, pin_memory=True)
-    h_unp = (torch.empty((chunk, L["unp_bytes"]), dtype=torch.uint8, pin_memory=True)
-             if eng.unpacked is not None else None)
+    host = [torch.empty((chunk, v.shape[1]), dtype=v.dtype, pin_memory=True) for _, v in ex]
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -366,48 +429,42 @@ def run_e2e(eng, c, run, stream, args):
         eng.step(n)
         idx = [(s + i) % eng.ring for i in range(n)]
         lo = idx[0]
-        if lo + n <= eng.ring:
-            h_obs[:n].copy_(eng.obs[lo:lo + n], non_blocking=True)
-            h_rew[:n].copy_(eng.reward[lo:lo + n], non_blocking=True)
-            h_done[:n].copy_(eng.done[lo:lo + n], non_blocking=True)
-            if h_unp is not None:
-                h_unp[:n].copy_(eng.unpacked[lo:lo + n], non_blocking=True)
-        else:
-            for j, sl in enumerate(idx):
-                h_obs[j].copy_(eng.obs[sl], non_blocking=True)
-                h_rew[j].copy_(eng.reward[sl], non_blocking=True)
-                h_done[j].copy_(eng.done[sl], non_blocking=True)
-                if h_unp is not None:
-                    h_unp[j].copy_(eng.unpacked[sl], non_blocking=True)
+        for (_, v), hb in zip(ex, host):
+            if lo + n <= eng.ring:
+                hb[:n].copy_(v[lo:lo + n], non_blocking=True)
+            else:
+                for j, sl in enumerate(idx):
+                    hb[j].copy_(v[sl], non_blocking=True)
         done_steps += n
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
-    d2h = L["obs_words"] * 8 + L["agents"] * 4 + eng.n_envs + (L["unp_bytes"] if h_unp is not None else 0)
     return {"value": eng.n_envs * n_steps / (ms / 1e3), "unit": "env-steps/s",
-            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(d2h),
-            "note": "per env-step: every env's obs, reward and done copied to pinned host memory"}
+            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(per_step),
+            "note": "per env-step: every output ring slot (%s) copied to pinned host memory"
+                    % ", ".join(k for k, _ in ex)}
 
 
 def _oracle_shard(job):
     """One host process of the multi-core oracle leg: its env range of the
     workload stepped for about `seconds`."""
-    n, base, seed, descs, unpacked, seconds = job
+    n, base, seed, descs, unpacked, seconds, flags = job
     sys.path.insert(0, ROOT)
     import oracle
 
-    w = oracle.World(n, seed, descs, env_id_base=base)
+    w = oracle.World(n, seed, descs, env_id_base=base, desync=bool(flags & H.HASE_DESYNC_START),
+                     fog=oracle_fog(flags))
     t = time.perf_counter()
     steps = 0
     while time.perf_counter() - t < seconds:
-        w.step(unpacked=unpacked)
+        oracle_step(w, flags, unpacked)
         steps += 1
     dt = time.perf_counter() - t
     w.close()
     return n, steps, dt
 
 
-def cpu_baseline(c, args, target_s=8.0):
+def cpu_baseline(c, args, flags=0, target_s=8.0):
     """The oracle (single-threaded C, as it stands) on a bounded sample of the
     same workload: all envs of the batch for as many steps as fit target_s,
     on one core and as one process per host core over env shards (spawned:
@@ -417,11 +474,11 @@ def cpu_baseline(c, args, target_s=8.0):
     import oracle
 
     n = c["n_envs"]
-    w = oracle.World(n, c["seed"], c["descs"])
+    w = oracle.World(n, c["seed"], c["descs"], desync=bool(flags & H.HASE_DESYNC_START), fog=oracle_fog(flags))
     t = time.perf_counter()
     steps = 0
     while time.perf_counter() - t < target_s:
-        w.step(unpacked=c["unpacked"])
+        oracle_step(w, flags, c["unpacked"])
         steps += 1
     dt = time.perf_counter() - t
     single = {"value": n * steps / dt, "unit": "env-steps/s", "cores": 1,
@@ -431,7 +488,7 @@ def cpu_baseline(c, args, target_s=8.0):
     for i in range(cores):
         lo, hi = i * n // cores, (i + 1) * n // cores
         d = c["descs"] if len(c["descs"]) == 1 else c["descs"][lo:hi]
-        jobs.append((hi - lo, lo, c["seed"], d, c["unpacked"], target_s))
+        jobs.append((hi - lo, lo, c["seed"], d, c["unpacked"], target_s, flags))
     try:
         with mp.get_context("spawn").Pool(cores) as pool:
             res = pool.map(_oracle_shard, jobs)
@@ -566,25 +623,26 @@ def run_reference(args):
         return
     if args.workload == "served":
         return run_reference_served(args, world)
-    c = workload(args.workload)
+    c, flags = apply_mode(workload(args.workload), args.mode)
     n = c["n_envs"]
+    desync, fog = bool(flags & H.HASE_DESYNC_START), oracle_fog(flags)
     # bounded sample: each benchmark step runs a sample of the rollout, sized
     # so that warmup + steps take about a minute in total
-    probe = oracle.World(n, c["seed"], c["descs"])
+    probe = oracle.World(n, c["seed"], c["descs"], desync=desync, fog=fog)
     t = time.perf_counter()
-    probe.step(unpacked=c["unpacked"])
+    oracle_step(probe, flags, c["unpacked"])
     per_env_step = (time.perf_counter() - t) / n
     budget = 60.0 / max(1, args.steps + args.warmup)
     sample_envs = max(1, min(n, int(budget / max(per_env_step, 1e-9))))
     sample_steps = 1
     w = oracle.World(sample_envs, c["seed"], c["descs"][:1] if len(c["descs"]) == 1 else
-                     c["descs"][:sample_envs])
+                     c["descs"][:sample_envs], desync=desync, fog=fog)
     for _ in range(args.warmup):
-        w.step(unpacked=c["unpacked"])
+        oracle_step(w, flags, c["unpacked"])
     t = time.perf_counter()
     for _ in range(args.steps):
         for _ in range(sample_steps):
-            w.step(unpacked=c["unpacked"])
+            oracle_step(w, flags, c["unpacked"])
     dt = time.perf_counter() - t
     value = sample_envs * sample_steps * args.steps / dt
     out = {
@@ -601,7 +659,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic (seeded Bernoulli maps, Philox actions)",
-        "config": {"workload": args.workload, "n_envs_per_gpu": n},
+        "config": {"workload": args.workload, "mode": args.mode, "flags": flags, "n_envs_per_gpu": n},
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
                          "sample": "%d of %d envs, 1 env-step per benchmark step" % (sample_envs, n)},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
@@ -617,6 +675,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ten1k", choices=sorted(RUN_STEPS))
+    ap.add_argument("--mode", default="default", choices=list(MODES),
+                    help="optional part of the step to include (observability modes, line of sight, "
+                         "desynchronised start, fog of war)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--run-steps", type=int, default=0,
                     help="override the env-steps per benchmark step (small profiling cases)")

@@ -242,15 +242,16 @@ class World:
         self._L.ho_observe(self._h, _p(obs), _p(unp))
         return (obs, unp) if unpacked else obs
 
-    def step(self, unpacked=False):
+    def step(self, unpacked=False, observe=True):
         """One step of every env; returns dict of obs, reward, done, action
-        (and unpacked when asked)."""
-        obs = np.zeros(self.obs_words, np.uint64)
+        (and unpacked when asked).  observe=False skips the decentralized
+        observation (its entry is then empty)."""
+        obs = np.zeros(self.obs_words if observe else 0, np.uint64)
         rew = np.zeros(self.n_agents_total, np.int32)
         done = np.zeros(self.n_envs, np.uint8)
         act = np.zeros(self.n_agents_total, np.uint8)
         unp = np.zeros(self.unp_bytes, np.uint8) if unpacked else None
-        self._L.ho_step(self._h, _p(obs), _p(rew), _p(done), _p(act), _p(unp))
+        self._L.ho_step(self._h, _p(obs) if observe else None, _p(rew), _p(done), _p(act), _p(unp))
         out = {"obs": obs, "reward": rew, "done": done, "action": act}
         if unpacked:
             out["unpacked"] = unp

@@ -85,23 +85,49 @@ __device__ __forceinline__ void obstacle_plane(const uint64_t* rows, int rw, int
 // rnd(i dy / n)) for i = 1 .. n-1, n = max(|dx|, |dy|), rnd rounding halves
 // away from zero -- is free in the window's obstacle plane (lo, hi), whose
 // out-of-grid cells are already set.
-__host__ __device__ inline int rnd_half_away(int p, int n) {
-    return p >= 0 ? (2 * p + n) / (2 * n) : -((-2 * p + n) / (2 * n));
+
+// The cells strictly between the centre and every window cell, per radius
+// 0..4 (window cell k of radius r at entry block_off(r) + k, where
+// block_off(r) = sum of (2r' + 1)^2 over r' < r; bits 0-63 in lo, 64-80 in
+// hi), evaluated by the compiler.
+__host__ __device__ constexpr int block_off(int r) { return (4 * r * r * r - r) / 3; }
+struct BlockerTable {
+    unsigned long long lo[165];
+    unsigned int hi[165];
+};
+constexpr int rnd_half_away_ce(int p, int n) { return p >= 0 ? (2 * p + n) / (2 * n) : -((-2 * p + n) / (2 * n)); }
+constexpr BlockerTable make_blockers() {
+    BlockerTable t{};
+    for (int r = 0; r <= 4; ++r) {
+        const int D = 2 * r + 1;
+        for (int dy = -r; dy <= r; ++dy) {
+            for (int dx = -r; dx <= r; ++dx) {
+                const int n = (dx < 0 ? -dx : dx) > (dy < 0 ? -dy : dy) ? (dx < 0 ? -dx : dx) : (dy < 0 ? -dy : dy);
+                const int e = block_off(r) + (dy + r) * D + (dx + r);
+                for (int i = 1; i < n; ++i) {
+                    const int k = (rnd_half_away_ce(i * dy, n) + r) * D + (rnd_half_away_ce(i * dx, n) + r);
+                    if (k < 64)
+                        t.lo[e] |= 1ull << k;
+                    else
+                        t.hi[e] |= 1u << (k - 64);
+                }
+            }
+        }
+    }
+    return t;
 }
+static __constant__ BlockerTable c_blockers = make_blockers();
 
 __device__ inline void window_visibility(uint64_t lo, uint64_t hi, int r, uint64_t& vlo, uint64_t& vhi) {
-    const int D = 2 * r + 1;
+    const int DD = (2 * r + 1) * (2 * r + 1), o = block_off(r);
     vlo = vhi = 0;
-    for (int dy = -r; dy <= r; ++dy) {
-        for (int dx = -r; dx <= r; ++dx) {
-            const int n = max(abs(dx), abs(dy));
-            bool vis = true;
-            for (int i = 1; i < n && vis; ++i) {
-                const int k = (rnd_half_away(i * dy, n) + r) * D + (rnd_half_away(i * dx, n) + r);
-                vis = !(((k < 64 ? lo : hi) >> (k & 63)) & 1ull);
-            }
-            if (vis) set_bit(vlo, vhi, (dy + r) * D + (dx + r));
-        }
+    for (int k = 0; k < DD; ++k) {
+        const uint64_t blocked = (lo & c_blockers.lo[o + k]) | (hi & (uint64_t)c_blockers.hi[o + k]);
+        const uint64_t vis = blocked == 0ull ? 1ull : 0ull;
+        if (k < 64)
+            vlo |= vis << k;
+        else
+            vhi |= vis << (k - 64);
     }
 }
 
@@ -186,6 +212,78 @@ __device__ inline void central_env(const EnvRT& E, const uint64_t* rows, const u
         out[2 * S + y] = seen & sk;
         out[3 * S + y] = seen & hd;
     }
+}
+
+// Row y of the centralized observation of one env without line of sight
+// (the four planes of central_env, one row of each).
+__device__ inline void central_row(const EnvRT& E, const uint64_t* rows, const uint16_t* src, uint32_t sh, int y,
+                                   uint64_t* out) {
+    const int S = E.side, A = E.n_agents, ns = E.n_seekers, rw = E.rw;
+    const uint32_t xmask = (1u << sh) - 1u;
+    const uint64_t smask = S == 64 ? ~0ull : ((1ull << S) - 1ull);
+    uint64_t seen = 0, sk = 0, hd = 0;
+    for (int a = 0; a < A; ++a) {
+        const uint32_t v = src[a] & 0x0fffu;
+        const int xa = (int)(v & xmask), ya = (int)(v >> sh);
+        const int team = a < ns ? 0 : 1;
+        if (ya == y) {
+            if (team == 0)
+                sk |= 1ull << xa;
+            else
+                hd |= 1ull << xa;
+        }
+        if (!team_sees(E, team)) continue;
+        const int R = team_radius(E, team), dy = y - ya;
+        if (dy < -R || dy > R) continue;
+        const uint64_t wrow = (1ull << (2 * R + 1)) - 1ull;
+        const int x0 = xa - R;
+        seen |= x0 >= 0 ? (wrow << x0) : (wrow >> (-x0));
+    }
+    seen &= smask;
+    const uint64_t* pr = rows + (y + kPad) * rw;
+    const uint64_t obst = (rw == 1 ? (pr[0] >> kPad) : ((pr[0] >> kPad) | (pr[1] << (64 - kPad)))) & smask;
+    out[y] = seen;
+    out[S + y] = seen & obst;
+    out[2 * S + y] = seen & sk;
+    out[3 * S + y] = seen & hd;
+}
+
+// Row y of the cells seen by agents a0..a1-1 of an env without line of
+// sight: the union of their window rows.  The constants of the env are
+// taken once (row_seen_ctx) and reused over the steps of a chunk.
+struct RowSeen {
+    uint64_t ws, wh, smask;  // window rows of the seekers / hiders, grid columns
+    uint32_t sh, xmask;
+    int ns, rs, rh;
+    bool s_sees, h_sees;
+};
+__device__ __forceinline__ RowSeen row_seen_ctx(const EnvRT& E) {
+    RowSeen c;
+    c.sh = cell_shift(E);
+    c.xmask = (1u << c.sh) - 1u;
+    c.ns = E.n_seekers;
+    c.rs = E.r_seek;
+    c.rh = E.r_hide;
+    c.ws = (1ull << (2 * c.rs + 1)) - 1ull;
+    c.wh = (1ull << (2 * c.rh + 1)) - 1ull;
+    c.smask = E.side == 64 ? ~0ull : ((1ull << E.side) - 1ull);
+    c.s_sees = team_sees(E, 0);
+    c.h_sees = team_sees(E, 1);
+    return c;
+}
+__device__ __forceinline__ uint64_t row_seen(const RowSeen& c, const uint16_t* src, int a0, int a1, int y) {
+    uint64_t seen = 0;
+    for (int a = a0; a < a1; ++a) {
+        const bool hider = a >= c.ns;
+        if (!(hider ? c.h_sees : c.s_sees)) continue;
+        const uint32_t v = src[a] & 0x0fffu;
+        const int R = hider ? c.rh : c.rs;
+        if ((uint32_t)(y - (int)(v >> c.sh) + R) > (uint32_t)(2 * R)) continue;
+        const int x0 = (int)(v & c.xmask) - R;
+        const uint64_t w = hider ? c.wh : c.ws;
+        seen |= x0 >= 0 ? (w << x0) : (w >> (-x0));
+    }
+    return seen & c.smask;
 }
 
 // Ally / opponent planes of agent a from the packed positions P[0..A)
@@ -1170,7 +1268,22 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                 else
                     emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
             }
-            if (P.central || P.st_cells) {  // centralized observation, true state
+            // the group is uniform in side, teams and radii
+            const bool row_central = P.central && !line_of_sight(H.env[0]);
+            if (row_central) {  // centralized observation, one thread per (step, env, row)
+                const uint32_t S = H.env[0].side, ne_ = (uint32_t)ne;
+                for (uint32_t it = (uint32_t)worker; it < C.len * ne_ * S; it += (uint32_t)n_workers) {
+                    const uint32_t ke = it / S, y = it - ke * S, k = ke / ne_, e = ke - k * ne_;
+                    const int first = L.first_slot[e];
+                    const uint16_t* Tk = C.T + k * nsl + first;
+                    const uint16_t* src = (Tk[0] & kDoneBit) ? H.p0 + first : Tk;
+                    uint32_t sl = C.base_slot + k;
+                    if (sl >= P.ring) sl -= P.ring;
+                    central_row(H.env[e], C.rows + L.rows_off[e], src, cell_shift(H.env[e]), (int)y,
+                                P.central + (uint64_t)sl * P.central_words + H.coff[e]);
+                }
+            }
+            if ((P.central && !row_central) || P.st_cells) {  // per (step, env)
                 const uint32_t ne_ = (uint32_t)ne;
                 for (uint32_t it = (uint32_t)worker; it < C.len * ne_; it += (uint32_t)n_workers) {
                     const uint32_t k = it / ne_, e = it - k * ne_;
@@ -1181,7 +1294,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                     const uint32_t sh = cell_shift(E);
                     uint32_t sl = C.base_slot + k;
                     if (sl >= P.ring) sl -= P.ring;
-                    if (P.central)
+                    if (P.central && !row_central)
                         central_env(E, C.rows + L.rows_off[e], src, sh,
                                     P.central + (uint64_t)sl * P.central_words + H.coff[e]);
                     if (P.st_cells) {  // the observed state: cells and the episode clock after the step
@@ -1195,37 +1308,45 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             // Fog of war: one thread per fog row (env, unit, row y) scans the
             // chunk's steps in order; an episode's first observation (a done
             // step: the reset state) starts the row afresh.
-            const bool per_agent = (L.flags & kFogAgent) != 0;
-            for (uint32_t u = (uint32_t)worker; u < fog_rows; u += (uint32_t)n_workers) {
-                const int e = fog_env_of(u);
-                const EnvRT& E = H.env[e];
-                const uint32_t S = E.side, sh = cell_shift(E);
-                const uint32_t rel = u - L.fog_off[e], j = rel / S, y = rel - j * S;
-                const int ns = E.n_seekers;
-                const int a0 = per_agent ? (team_sees(E, 0) ? (int)j : ns + (int)j) : 0;
-                const int a1 = per_agent ? a0 + 1 : (int)E.n_agents;
-                const int first = L.first_slot[e];
-                const uint64_t* rows_e = C.rows + L.rows_off[e];
-                uint64_t* out = P.fog + H.foff[e] + j * 2u * S + y;
-                uint64_t disc = s_fog[u];
-                for (uint32_t k = 0; k < C.len; ++k) {
-                    const uint16_t* Tk = C.T + k * nsl + first;
-                    const bool done = (Tk[0] & kDoneBit) != 0u;
-                    const uint16_t* src = done ? H.p0 + first : Tk;
-                    uint64_t seen = 0;
-                    for (int a = a0; a < a1; ++a) {
-                        const int team = a < ns ? 0 : 1;
-                        if (team_sees(E, team)) seen |= agent_seen_row(E, rows_e, src[a] & 0x0fffu, sh, team, (int)y);
+            if (fog_rows) {
+                const bool per_agent = (L.flags & kFogAgent) != 0;
+                const bool los = line_of_sight(H.env[0]);  // uniform in the group
+                for (uint32_t u = (uint32_t)worker; u < fog_rows; u += (uint32_t)n_workers) {
+                    const int e = fog_env_of(u);
+                    const EnvRT& E = H.env[e];
+                    const uint32_t S = E.side, rel = u - L.fog_off[e], j = rel / S, y = rel - j * S;
+                    const int ns = E.n_seekers;
+                    const int a0 = per_agent ? (team_sees(E, 0) ? (int)j : ns + (int)j) : 0;
+                    const int a1 = per_agent ? a0 + 1 : (int)E.n_agents;
+                    const int first = L.first_slot[e];
+                    const uint64_t* rows_e = C.rows + L.rows_off[e];
+                    const RowSeen rs = row_seen_ctx(E);
+                    uint64_t* out = P.fog + H.foff[e] + j * 2u * S + y;
+                    uint64_t disc = s_fog[u];
+                    uint32_t sl = C.base_slot;
+                    for (uint32_t k = 0; k < C.len; ++k) {
+                        const uint16_t* Tk = C.T + k * nsl + first;
+                        const bool done = (Tk[0] & kDoneBit) != 0u;
+                        const uint16_t* src = done ? H.p0 + first : Tk;
+                        uint64_t seen = 0;
+                        if (los) {
+                            for (int a = a0; a < a1; ++a) {
+                                const int team = a < ns ? 0 : 1;
+                                if (team_sees(E, team))
+                                    seen |= agent_seen_row(E, rows_e, src[a] & 0x0fffu, rs.sh, team, (int)y);
+                            }
+                        } else {
+                            seen = row_seen(rs, src, a0, a1, (int)y);
+                        }
+                        const uint64_t prev = done ? 0ull : disc;
+                        disc = prev | seen;
+                        uint64_t* o = out + (uint64_t)sl * P.fog_words;
+                        o[0] = disc;
+                        o[S] = seen & ~prev;
+                        if (++sl == P.ring) sl = 0;
                     }
-                    const uint64_t prev = done ? 0ull : disc;
-                    disc = prev | seen;
-                    uint32_t sl = C.base_slot + k;
-                    if (sl >= P.ring) sl -= P.ring;
-                    uint64_t* o = out + (uint64_t)sl * P.fog_words;
-                    o[0] = disc;
-                    o[S] = seen & ~prev;
+                    s_fog[u] = disc;
                 }
-                s_fog[u] = disc;
             }
         }
         // a1 for chunk c + 1
