@@ -216,6 +216,18 @@ def test_fog_of_war_checkpoint_resume():
     b.close()
 
 
+@pytest.mark.parametrize("desc,flags", [
+    (W.env_desc(6, 3, 2, 1, 2, 1, "0.2"), hase.HASE_EXPORT_FOG | hase.HASE_EXPORT_CENTRAL | hase.HASE_EXPORT_STATE),
+    (W.env_desc(2, 3, 1, 2, 1, 5, "0.5"), hase.HASE_EXPORT_FOG | hase.HASE_FOG_PER_AGENT | hase.HASE_EXPORT_CENTRAL),
+    (W.env_desc(12, 6, 3, 0, 0, 9, "0.2", 3 | 4), hase.HASE_EXPORT_FOG | hase.HASE_EXPORT_CENTRAL),
+    (W.env_desc(64, 16, 8, 4, 4, 17, "0.3", 3 | 4), hase.HASE_EXPORT_FOG | hase.HASE_FOG_PER_AGENT | hase.HASE_SKIP_OBS),
+    (W.env_desc(10, 4, 2, 2, 2, 30, 2**32 - 1, 1), hase.HASE_EXPORT_FOG | hase.HASE_EXPORT_STATE | hase.HASE_SKIP_OBS),
+    (W.env_desc(16, 6, 3, 3, 2, 30, "0.2"), hase.HASE_EXPORT_STATE | hase.HASE_EXPORT_UNPACKED | hase.HASE_DESYNC_START),
+], ids=["cap1-all-exports", "smallest-grid", "radius0-los", "largest-los-per-agent", "all-blocked", "state-unpacked"])
+def test_optional_exports_edge_cases(desc, flags):
+    compare_run(9, 77, [desc], 40, flags=flags | hase.HASE_EXPORT_ACTIONS, launches=[1, 17, 22], chunk_steps=8)
+
+
 def test_ring_wraparound_and_split_launches():
     c = W.ten1k()
     compare_run(64, c["seed"], c["descs"], 300, ring=7, launches=[1, 2, 97, 200])
