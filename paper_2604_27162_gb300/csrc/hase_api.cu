@@ -230,7 +230,13 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
         if (g.n_envs == 0) return false;  // one env alone exceeds the budget
         uint16_t flags = h->fog_flags;
         plan_group(genv.data(), g.n_envs, (int)h->kc, flags | kUseTable, plan);
-        if (plan.total <= h->smem_budget) flags |= kUseTable;
+        const int fam0 = family_of(genv[0]);
+        if (plan.total <= h->smem_budget) {
+            flags |= kUseTable;
+        } else if (fam0 >= 9) {  // line-of-sight families: one table for both radii
+            plan_group(genv.data(), g.n_envs, (int)h->kc, flags | kUseTable | kSharedTable, plan);
+            if (plan.total <= h->smem_budget) flags |= kUseTable | kSharedTable;
+        }
         plan_group(genv.data(), g.n_envs, (int)h->kc, flags, plan);
         g.flags = flags;
         g.n_dyn = (uint8_t)plan.n_dyn;

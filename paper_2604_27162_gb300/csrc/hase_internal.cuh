@@ -59,6 +59,8 @@ struct EnvState {
 constexpr uint16_t kUseTable = 1;   // obstacle plane from per-cell window tables
 constexpr uint16_t kFog = 2;        // fog-of-war maps (one unit per env)
 constexpr uint16_t kFogAgent = 4;   // with kFog: one unit per observing agent
+constexpr uint16_t kSharedTable = 8;  // with kUseTable: one table of the larger emitting radius
+                                      // serves both teams (line-of-sight families)
 
 // All envs of a group share the radii, the emitting teams, the row width and
 // the agent and seeker counts, so one code path serves the whole CTA.
@@ -112,20 +114,28 @@ struct GroupPlan {
 };
 
 // One thread emits a whole (step, env) when the seekers are the first
-// ceil(A / 2) agents (windows of up to two words a plane) and no line of
-// sight masks the windows; other shapes take the lane-per-agent emission.
+// ceil(A / 2) agents (windows of up to two words a plane; with line of
+// sight, of one word); other shapes take the lane-per-agent emission.
 __host__ __device__ inline bool fast_emission(const EnvRT& E) {
-    return E.wpp <= 2 && E.n_seekers == (E.n_agents + 1u) / 2u && !(E.obs_teams & kObsLos);
+    return E.wpp <= 2 && E.n_seekers == (E.n_agents + 1u) / 2u && (!(E.obs_teams & kObsLos) || E.wpp <= 1);
 }
 
 // Kernel families: family 0 runs the general (lane per agent) emission;
 // families 1..4 the one-thread emission for A in 1-4, 5-8, 9-12, 13-16 with
-// one word a plane, families 5..8 the same with two words a plane (radius 4).
-// Each group is launched with the kernel of its family.
-constexpr int kFamilies = 9;
+// one word a plane, families 5..8 the same with two words a plane (radius 4),
+// families 9..12 the one-word forms with line of sight.  Each group is
+// launched with the kernel of its family.
+constexpr int kFamilies = 13;
 __host__ __device__ inline int family_of(const EnvRT& E) {
     if (!fast_emission(E)) return 0;
+    if (E.obs_teams & kObsLos) return 9 + ((int)E.n_agents - 1) / 4;
     return (E.wpp == 2 ? 5 : 1) + ((int)E.n_agents - 1) / 4;
+}
+
+// Radius of the shared window table: the larger emitting radius.
+__host__ __device__ inline int table_radius(const EnvRT& E) {
+    const int rs = team_emits(E, 0) ? (int)E.r_seek : 0, rh = team_emits(E, 1) ? (int)E.r_hide : 0;
+    return rs > rh ? rs : rh;
 }
 
 // Fog-of-war units of an env: all observing agents together, or each
@@ -163,12 +173,13 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
         for (int t = 0; t < 2; ++t) {
             G.tbl_off[i][t] = ~0u;
             if (!(flags & kUseTable) || !team_emits(E, t)) continue;
-            if (t == 1 && team_emits(E, 0) && E.r_hide == E.r_seek) {
+            if (t == 1 && team_emits(E, 0) && (E.r_hide == E.r_seek || (flags & kSharedTable))) {
                 G.tbl_off[i][1] = G.tbl_off[i][0];
                 continue;
             }
             G.tbl_off[i][t] = to;
-            to += (uint32_t)E.side * E.side * table_words(E, team_radius(E, t));
+            const int r = (flags & kSharedTable) ? table_radius(E) : team_radius(E, t);
+            to += (uint32_t)E.side * E.side * table_words(E, r);
         }
     }
     G.fog_off[n] = fo;

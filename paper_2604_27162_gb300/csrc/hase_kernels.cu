@@ -378,6 +378,10 @@ HASE_FAMILY_DECL(5)
 HASE_FAMILY_DECL(6)
 HASE_FAMILY_DECL(7)
 HASE_FAMILY_DECL(8)
+HASE_FAMILY_DECL(9)
+HASE_FAMILY_DECL(10)
+HASE_FAMILY_DECL(11)
+HASE_FAMILY_DECL(12)
 #undef HASE_FAMILY_DECL
 
 // Opt in, once per device and outside any capture, to all the dynamic shared
@@ -393,8 +397,8 @@ cudaError_t prepare_step(uint32_t smem) {
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if ((int)smem + 8 * 1024 > optin) return cudaErrorInvalidValue;
-    cudaError_t (*opt[])(int) = {opt_in_f0, opt_in_f1, opt_in_f2, opt_in_f3, opt_in_f4,
-                                 opt_in_f5, opt_in_f6, opt_in_f7, opt_in_f8};
+    cudaError_t (*opt[])(int) = {opt_in_f0, opt_in_f1, opt_in_f2,  opt_in_f3,  opt_in_f4,  opt_in_f5, opt_in_f6,
+                                 opt_in_f7, opt_in_f8, opt_in_f9, opt_in_f10, opt_in_f11, opt_in_f12};
     for (auto f : opt)
         if ((e = f(optin)) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = 1;
@@ -415,6 +419,10 @@ cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint
         case 6: return launch_f6(p, n_groups, threads, smem, st);
         case 7: return launch_f7(p, n_groups, threads, smem, st);
         case 8: return launch_f8(p, n_groups, threads, smem, st);
+        case 9: return launch_f9(p, n_groups, threads, smem, st);
+        case 10: return launch_f10(p, n_groups, threads, smem, st);
+        case 11: return launch_f11(p, n_groups, threads, smem, st);
+        case 12: return launch_f12(p, n_groups, threads, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -610,6 +610,7 @@ struct TeamCtx {
     const SlotRec* slot;  // slot records of the env's agents
     uint32_t sh, xmask, side, rw;
     int ai0;              // emitting index of agent 0 of the team base
+    uint32_t tr;          // radius of the table's windows (> R: the team cuts its window out)
     bool use_table;
     bool v16;             // the env's obs words start 16-byte aligned
 };
@@ -665,7 +666,19 @@ __device__ __forceinline__ void unpack_planes_wide(uint8_t* u, const Words3& w, 
     }
 }
 
-template <int A, bool TA, bool HI, bool W2>
+// The inner (2 rs + 1)^2 window of a (2 rb + 1)^2 window plane (rb <= 3)
+// centred on the same cell.  A smaller window's obstacle and visibility bits
+// equal the inner part of the larger one's: its cells, and the cells between
+// them and the centre, all lie inside it.
+__device__ __forceinline__ uint64_t sub_window(uint64_t w, uint32_t rb, uint32_t rs) {
+    const uint32_t db = 2u * rb + 1u, ds = 2u * rs + 1u, off = rb - rs;
+    const uint64_t m = (1ull << ds) - 1ull;
+    uint64_t out = 0;
+    for (uint32_t i = 0; i < ds; ++i) out |= ((w >> ((i + off) * db + off)) & m) << (i * ds);
+    return out;
+}
+
+template <int A, bool TA, bool HI, bool W2, bool LOS>
 __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32_t R, uint32_t D, uint32_t KR,
                                                  uint32_t C2, uint32_t KP, uint32_t centre, uint32_t centre_hi,
                                                  const uint32_t (&X4)[(A + 3) / 4], const uint32_t (&Y4)[(A + 3) / 4],
@@ -718,12 +731,21 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
     w.oph = op2;
     w.o0 = 0;
     w.o0h = 0;
-    {  // a5 obstacle plane
+    {  // a5 obstacle plane (and, with line of sight, the visible cells)
+        uint64_t vis = ~0ull;
         if (T.use_table) {
             if (W2 && R == 4u) {  // two table words a cell
                 const uint64_t* c = T.tbl + 2u * (ya * T.side + xa);
                 w.o0 = c[0];
                 w.o0h = (uint32_t)c[1];
+            } else if (LOS) {  // one-word windows: obstacle plane, then visibility
+                const uint64_t* c = T.tbl + 2u * (ya * T.side + xa);
+                w.o0 = c[0];
+                vis = c[1];
+                if (T.tr != R) {  // a shared table of a larger radius: the inner window
+                    w.o0 = sub_window(w.o0, T.tr, R);
+                    vis = sub_window(vis, T.tr, R);
+                }
             } else {
                 w.o0 = T.tbl[ya * T.side + xa];
             }
@@ -731,6 +753,15 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
             uint64_t hi;
             obstacle_plane(T.rows, (int)T.rw, (int)xa, (int)ya, (int)R, w.o0, hi);
             w.o0h = (uint32_t)hi;
+            if (LOS) {
+                uint64_t vh;
+                window_visibility(w.o0, hi, (int)R, vis, vh);
+            }
+        }
+        if (LOS) {  // hidden cells read 0 in all three planes (one-word windows)
+            w.o0 &= vis;
+            w.al &= vis;
+            w.op &= vis;
         }
         if (T.unp) {
             if (W2)
@@ -750,7 +781,7 @@ __device__ __forceinline__ void st16(uint64_t* p, uint64_t a, uint64_t b) {
 // words of two consecutive observers leave as three 16-byte stores, and a
 // lone observer as one 16-byte and one 8-byte store; otherwise three 8-byte
 // stores per observer.
-template <int A, bool TA, bool HI, bool W2>
+template <int A, bool TA, bool HI, bool W2, bool LOS>
 __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, const uint32_t (&X4)[(A + 3) / 4],
                                                const uint32_t (&Y4)[(A + 3) / 4], const uint32_t (&P4)[(A + 3) / 4],
                                                const uint32_t (&P8)[(A + 3) / 4], uint32_t (&seenf)[(A + 3) / 4]) {
@@ -765,7 +796,7 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
 #pragma unroll 1
         for (int a = first; a < end; ++a) {
             const Words3 p =
-                observer_words<A, TA, HI, W2>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
+                observer_words<A, TA, HI, W2, LOS>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
             uint64_t* o = T.ob + 6 * (a - T.ai0);
             if (T.v16) {
                 st16(o, p.o0, p.o0h);
@@ -784,11 +815,11 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
 #pragma unroll 1
         for (int a = first; a < end;) {
             const Words3 p =
-                observer_words<A, TA, HI, W2>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
+                observer_words<A, TA, HI, W2, LOS>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
             const int w = 3 * (a - T.ai0);
             uint64_t* o = T.ob + w;
             if (T.v16 && !(w & 1) && a + 1 < end) {
-                const Words3 q = observer_words<A, TA, HI, W2>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4,
+                const Words3 q = observer_words<A, TA, HI, W2, LOS>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4,
                                                                P4, P8, seenf);
                 st16(o, p.o0, p.al);
                 st16(o + 2, p.op, q.o0);
@@ -812,7 +843,7 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
     }
 }
 
-template <int A, bool W2>
+template <int A, bool W2, bool LOS>
 __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const CtaShared& H, const EmitCtx& C,
                                                   uint32_t k, uint32_t e) {
     constexpr int NS = (A + 1) / 2, NW = (A + 3) / 4;
@@ -863,24 +894,26 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
         T.use_table = L.flags & kUseTable;
         T.v16 = (reinterpret_cast<uintptr_t>(T.ob) & 15u) == 0u;
         T.tbl = C.tbl + L.tbl_off[e][0];
+        T.tr = (L.flags & kSharedTable) ? (uint32_t)table_radius(E) : rs;
         T.ai0 = 0;
         if (emit_s) {
             if (W2)
-                emit_team_fast<A, false, true, true>(T, rs, X4, Y4, Ps, Ps8, seenf);
+                emit_team_fast<A, false, true, true, LOS>(T, rs, X4, Y4, Ps, Ps8, seenf);
             else if (Ds * Ds > 32u)
-                emit_team_fast<A, false, true, false>(T, rs, X4, Y4, Ps, Ps8, seenf);
+                emit_team_fast<A, false, true, false, LOS>(T, rs, X4, Y4, Ps, Ps8, seenf);
             else
-                emit_team_fast<A, false, false, false>(T, rs, X4, Y4, Ps, Ps8, seenf);
+                emit_team_fast<A, false, false, false, LOS>(T, rs, X4, Y4, Ps, Ps8, seenf);
         }
         if (emit_h) {
             T.tbl = C.tbl + L.tbl_off[e][1];
+            T.tr = (L.flags & kSharedTable) ? (uint32_t)table_radius(E) : rh;
             T.ai0 = emit_s ? 0 : NS;
             if (W2)
-                emit_team_fast<A, true, true, true>(T, rh, X4, Y4, Ph, Ph8, seenf);
+                emit_team_fast<A, true, true, true, LOS>(T, rh, X4, Y4, Ph, Ph8, seenf);
             else if (Dh * Dh > 32u)
-                emit_team_fast<A, true, true, false>(T, rh, X4, Y4, Ph, Ph8, seenf);
+                emit_team_fast<A, true, true, false, LOS>(T, rh, X4, Y4, Ph, Ph8, seenf);
             else
-                emit_team_fast<A, true, false, false>(T, rh, X4, Y4, Ph, Ph8, seenf);
+                emit_team_fast<A, true, false, false, LOS>(T, rh, X4, Y4, Ph, Ph8, seenf);
         }
     }
     uint32_t seen = 0;
@@ -914,14 +947,14 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
     }
 }
 
-template <int A, bool W2>
+template <int A, bool W2, bool LOS>
 __device__ __forceinline__ void emit_segments_fast(const StepParams& P, const CtaShared& H, const EmitCtx& C) {
     const uint32_t ne = H.plan.n_envs;
     const uint32_t total = C.len * ne;
     const uint32_t dk = (uint32_t)C.n_workers / ne, de = (uint32_t)C.n_workers % ne;
     uint32_t k = (uint32_t)C.worker / ne, e = (uint32_t)C.worker % ne;
     for (uint32_t it = (uint32_t)C.worker; it < total; it += (uint32_t)C.n_workers) {
-        emit_segment_fast<A, W2>(P, H, C, k, e);
+        emit_segment_fast<A, W2, LOS>(P, H, C, k, e);
         e += de;
         k += dk;
         if (e >= ne) {
@@ -936,11 +969,12 @@ template <int FAM>
 __device__ __forceinline__ void emit_fast_dispatch(int A, const StepParams& P, const CtaShared& H,
                                                    const EmitCtx& C) {
     constexpr int a0 = 4 * ((FAM - 1) % 4) + 1;
-    constexpr bool W2 = FAM > 4;
-    if (A == a0) emit_segments_fast<a0, W2>(P, H, C);
-    else if (A == a0 + 1) emit_segments_fast<a0 + 1, W2>(P, H, C);
-    else if (A == a0 + 2) emit_segments_fast<a0 + 2, W2>(P, H, C);
-    else emit_segments_fast<a0 + 3, W2>(P, H, C);
+    constexpr bool W2 = FAM >= 5 && FAM <= 8;  // two words a plane
+    constexpr bool LOS = FAM >= 9;             // line of sight, one word a plane
+    if (A == a0) emit_segments_fast<a0, W2, LOS>(P, H, C);
+    else if (A == a0 + 1) emit_segments_fast<a0 + 1, W2, LOS>(P, H, C);
+    else if (A == a0 + 2) emit_segments_fast<a0 + 2, W2, LOS>(P, H, C);
+    else emit_segments_fast<a0 + 3, W2, LOS>(P, H, C);
 }
 
 // Per-cell shared state of the dynamics: a claim word (byte a-1 holds the
@@ -1052,7 +1086,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             for (int t = 0; t < 2; ++t) {
                 if (L.tbl_off[i][t] == ~0u) continue;
                 if (t == 1 && L.tbl_off[i][1] == L.tbl_off[i][0]) continue;
-                const int r = team_radius(E, t);
+                const int r = (L.flags & kSharedTable) ? table_radius(E) : team_radius(E, t);
                 const uint32_t W = words_of_radius(r), Wt = table_words(E, r);
                 const bool los = line_of_sight(E);
                 uint64_t* Tb = s_tbl + L.tbl_off[i][t];

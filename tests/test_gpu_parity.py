@@ -108,6 +108,8 @@ def test_desynchronised_start_matches_oracle():
     W.env_desc(24, 7, 4, 4, 4, 40, "0.25", 3 | 4),     # one-thread emission, radius 4 (two words)
     W.env_desc(16, 6, 2, 3, 1, 30, "0.3", 3 | 4),      # lane-per-agent emission
     W.env_desc(12, 5, 3, 2, 2, 30, "0.2", 2 | 4),      # hiders only emit
+    W.env_desc(10, 3, 2, 2, 3, 30, "0.2", 1 | 4),      # one-thread emission, 1-4 agents
+    W.env_desc(20, 16, 8, 3, 1, 30, "0.25", 3 | 4),    # one-thread emission, 13-16 agents
 ])
 def test_line_of_sight_matches_oracle(desc):
     compare_run(36, 17, [desc], 70, flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED)
@@ -127,6 +129,15 @@ def test_centralized_observation_matches_oracle(desc):
 
 def test_centralized_observation_uneven():
     compare_run(30, 24, W.uneven_descs(30, 12), 45, flags=hase.HASE_EXPORT_CENTRAL, launches=[20, 25])
+
+
+def test_line_of_sight_shared_table():
+    """Seven 32x32 envs per CTA: the per-team window tables (radius 3 and 2,
+    with visibility) do not fit, one radius-3 table serves both teams."""
+    desc = W.env_desc(32, 10, 5, 3, 2, 40, "0.2", 3 | 4)
+    compare_run(21, 23, [desc], 75, flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED,
+                max_group_envs=7, launches=[40, 35])
+    compare_run(21, 24, [W.env_desc(32, 7, 4, 1, 3, 30, "0.3", 3 | 4)], 50, max_group_envs=7)
 
 
 def test_line_of_sight_uneven():
@@ -360,6 +371,12 @@ def test_full_size_ten_agents_sampled():
 def test_full_size_single_agent_sampled():
     cfg = W.single1k()
     _full_size_check(cfg, 3000, [0, 5, 700, 1023], flags=hase.HASE_EXPORT_UNPACKED)
+
+
+def test_full_size_line_of_sight_sampled():
+    cfg = W.ten1k()
+    cfg = dict(cfg, descs=[dict(cfg["descs"][0], obs_teams=3 | 4)])
+    _full_size_check(cfg, 1500, [0, 338, 1023])
 
 
 def test_full_size_uneven_sampled():
