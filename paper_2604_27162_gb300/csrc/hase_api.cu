@@ -58,7 +58,7 @@ struct hase_handle {
     std::vector<uint64_t> fog_off;
     std::vector<uint32_t> fog_off32;
     uint64_t fog_words = 0;
-    uint16_t fog_flags = 0;  // group flags kFog | kFogAgent
+    uint16_t base_flags = 0;  // group flags from the config: kFog, kFogAgent, kCentral
     uint64_t* d_fog = nullptr;
     uint32_t* d_fog_off = nullptr;
     uint64_t* d_fog_state = nullptr;
@@ -217,7 +217,7 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             if (g.n_slots + En.n_agents > (uint32_t)kMaxGroupSlots) break;
             if (many && g.n_slots + En.n_agents > 32u) break;
             genv.push_back(En);
-            const uint16_t flags = h->fog_flags;
+            const uint16_t flags = h->base_flags;
             if (!plan_group(genv.data(), (int)genv.size(), (int)h->kc, flags, plan) ||
                 plan.total > h->smem_budget) {
                 genv.pop_back();
@@ -228,7 +228,7 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             ++i;
         }
         if (g.n_envs == 0) return false;  // one env alone exceeds the budget
-        uint16_t flags = h->fog_flags;
+        uint16_t flags = h->base_flags;
         plan_group(genv.data(), g.n_envs, (int)h->kc, flags | kUseTable, plan);
         const int fam0 = family_of(genv[0]);
         if (plan.total <= h->smem_budget) {
@@ -356,12 +356,13 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     h->fog_off.assign(h->n_envs + 1, 0);
     if (h->flags & HASE_EXPORT_FOG) {
         const bool per_agent = (h->flags & HASE_FOG_PER_AGENT) != 0u;
-        h->fog_flags = (uint16_t)(kFog | (per_agent ? kFogAgent : 0u));
+        h->base_flags = (uint16_t)(kFog | (per_agent ? kFogAgent : 0u));
         for (uint32_t e = 0; e < h->n_envs; ++e)
             h->fog_off[e + 1] = h->fog_off[e] + 2ull * fog_units(h->env[e], per_agent) * h->env[e].side;
         h->fog_words = h->fog_off[h->n_envs];
         h->fog_off32.assign(h->fog_off.begin(), h->fog_off.end() - 1);
     }
+    if (h->flags & HASE_EXPORT_CENTRAL) h->base_flags |= kCentral;  // base group flags
     if (h->obs_words > 0xffffffffull || h->agents > 0xffffffffull || h->unp_bytes > 0xffffffffull ||
         h->central_words > 0xffffffffull || h->fog_words > 0xffffffffull) {
         delete h;

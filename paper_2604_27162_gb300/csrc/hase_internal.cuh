@@ -26,6 +26,7 @@ constexpr int kMaxGroupEnvs = 64;     // envs per CTA
 constexpr int kMaxGroupSlots = 128;   // agents per CTA (four dynamics warps)
 constexpr int kMaxDyn = 4;            // dynamics warps per CTA
 constexpr int kMaxChunk = 64;         // steps per on-chip chunk
+constexpr int kMaxEmitWarps = 12;     // emission warps per CTA
 constexpr int kObsHiders = 2;         // obs_teams value: only hiders emit
 constexpr uint32_t kObsLos = 4;       // obs_teams bit: line of sight masks the windows
 constexpr uint32_t kObsNoDec = 8;     // obs_teams bit: no decentralized planes are written
@@ -61,6 +62,7 @@ constexpr uint16_t kFog = 2;        // fog-of-war maps (one unit per env)
 constexpr uint16_t kFogAgent = 4;   // with kFog: one unit per observing agent
 constexpr uint16_t kSharedTable = 8;  // with kUseTable: one table of the larger emitting radius
                                       // serves both teams (line-of-sight families)
+constexpr uint16_t kCentral = 16;     // centralized observation: two row buffers per emission warp
 
 // All envs of a group share the radii, the emitting teams, the row width and
 // the agent and seeker counts, so one code path serves the whole CTA.
@@ -109,7 +111,7 @@ struct GroupPlan {
     uint32_t n_envs;
     uint32_t n_slots;
     uint32_t act_words;                  // uint32 words per action buffer
-    uint32_t act, traj, rows, claim, tbl, state, fog, total;  // byte offsets
+    uint32_t act, traj, rows, claim, tbl, state, fog, cen, total;  // byte offsets
     uint16_t flags;
 };
 
@@ -196,7 +198,9 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
     G.tbl = align_up(G.claim + co * 4, 16);
     G.state = G.tbl + to * 8;                            // uint8 per cell
     G.fog = align_up(G.state + co, 16);                  // uint64 per fog row
-    G.total = align_up(G.fog + fo * 8, 16);
+    G.cen = align_up(G.fog + fo * 8, 16);                // uint64 [emit warps][2][4][side]
+    const uint32_t cen_words = (flags & kCentral) && n ? kMaxEmitWarps * 8u * envs[0].side : 0u;
+    G.total = align_up(G.cen + cen_words * 8, 16);
     G.flags = flags;
     return true;
 }

@@ -214,38 +214,84 @@ __device__ inline void central_env(const EnvRT& E, const uint64_t* rows, const u
     }
 }
 
-// Row y of the centralized observation of one env without line of sight
-// (the four planes of central_env, one row of each).
-__device__ inline void central_row(const EnvRT& E, const uint64_t* rows, const uint16_t* src, uint32_t sh, int y,
-                                   uint64_t* out) {
+// OR of a row into a shared-memory row word, as native 32-bit atomics on
+// its halves (the upper half only for grids over 32 columns).
+__device__ __forceinline__ void or_row(uint64_t* w, uint64_t bits, bool wide) {
+    unsigned* h = reinterpret_cast<unsigned*>(w);
+    if ((uint32_t)bits) atomicOr(h, (unsigned)bits);
+    if (wide && (bits >> 32)) atomicOr(h + 1, (unsigned)(bits >> 32));
+}
+
+// Bulk asynchronous copies from shared to global memory (the untiled
+// cp.async.bulk: both addresses 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Wait until at most one copy group still reads its shared source.
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// Wait until every copy group has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Order this thread's shared-memory writes before later bulk copies read them.
+__device__ __forceinline__ void fence_smem_to_bulk() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Centralized observation of one (step, env) by one warp (all lanes), built
+// in a buffer of 4 S words of shared memory laid out as the output block
+// ([4][S]: seen, seen obstacles, seen seekers, seen hiders).  Lane a (< A)
+// ORs its cell into the seeker or hider rows (words 2S.., 3S..) and, if its
+// team observes, its window rows (with line of sight: only the visible
+// cells, from one visibility mask) into the seen rows; then lane y turns
+// row y of each plane into its output value in place, and lane 0 copies the
+// block to global memory with one bulk copy (no generic stores, so the
+// warp's next __syncwarp does not wait for them).  The caller makes sure
+// the buffer is no longer read by an earlier copy.
+__device__ inline void central_warp(const EnvRT& E, const uint64_t* rows, const uint16_t* src, uint32_t sh,
+                                    int lane, uint64_t* buf, uint64_t* out) {
     const int S = E.side, A = E.n_agents, ns = E.n_seekers, rw = E.rw;
-    const uint32_t xmask = (1u << sh) - 1u;
     const uint64_t smask = S == 64 ? ~0ull : ((1ull << S) - 1ull);
-    uint64_t seen = 0, sk = 0, hd = 0;
-    for (int a = 0; a < A; ++a) {
-        const uint32_t v = src[a] & 0x0fffu;
-        const int xa = (int)(v & xmask), ya = (int)(v >> sh);
-        const int team = a < ns ? 0 : 1;
-        if (ya == y) {
-            if (team == 0)
-                sk |= 1ull << xa;
-            else
-                hd |= 1ull << xa;
+    for (int y = lane; y < 4 * S; y += 32) buf[y] = 0ull;
+    __syncwarp();
+    if (lane < A) {
+        const uint32_t v = src[lane] & 0x0fffu;
+        const int xa = (int)(v & ((1u << sh) - 1u)), ya = (int)(v >> sh);
+        const int team = lane < ns ? 0 : 1;
+        const bool wide = S > 32;
+        or_row(buf + (team ? 3 * S : 2 * S) + ya, 1ull << xa, wide);
+        if (team_sees(E, team)) {
+            const int R = team_radius(E, team);
+            const uint64_t wfull = (1ull << (2 * R + 1)) - 1ull;
+            uint64_t vl = 0, vh = 0;
+            const bool los = line_of_sight(E);
+            if (los) {
+                uint64_t lo, hi;
+                obstacle_plane(rows, rw, xa, ya, R, lo, hi);
+                window_visibility(lo, hi, R, vl, vh);
+            }
+            const int x0 = xa - R;
+            for (int dy = -R; dy <= R; ++dy) {
+                const int y = ya + dy;
+                if (y < 0 || y >= S) continue;
+                const uint64_t w = los ? (wfull & window_row(vl, vh, R, dy)) : wfull;
+                const uint64_t bits = (x0 >= 0 ? (w << x0) : (w >> (-x0))) & smask;
+                or_row(buf + y, bits, wide);
+            }
         }
-        if (!team_sees(E, team)) continue;
-        const int R = team_radius(E, team), dy = y - ya;
-        if (dy < -R || dy > R) continue;
-        const uint64_t wrow = (1ull << (2 * R + 1)) - 1ull;
-        const int x0 = xa - R;
-        seen |= x0 >= 0 ? (wrow << x0) : (wrow >> (-x0));
     }
-    seen &= smask;
-    const uint64_t* pr = rows + (y + kPad) * rw;
-    const uint64_t obst = (rw == 1 ? (pr[0] >> kPad) : ((pr[0] >> kPad) | (pr[1] << (64 - kPad)))) & smask;
-    out[y] = seen;
-    out[S + y] = seen & obst;
-    out[2 * S + y] = seen & sk;
-    out[3 * S + y] = seen & hd;
+    __syncwarp();
+    for (int y = lane; y < S; y += 32) {  // each lane reads, then rewrites, only row y
+        const uint64_t seen = buf[y];
+        const uint64_t* pr = rows + (y + kPad) * rw;
+        const uint64_t obst = (rw == 1 ? (pr[0] >> kPad) : ((pr[0] >> kPad) | (pr[1] << (64 - kPad)))) & smask;
+        const uint64_t sk = buf[2 * S + y], hd = buf[3 * S + y];
+        buf[S + y] = seen & obst;
+        buf[2 * S + y] = seen & sk;
+        buf[3 * S + y] = seen & hd;
+    }
+    fence_smem_to_bulk();
+    __syncwarp();
+    if (lane == 0) bulk_store(out, buf, 32u * (uint32_t)S);
 }
 
 // Row y of the cells seen by agents a0..a1-1 of an env without line of
@@ -1281,6 +1327,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
     const int n_workers = M * 32;
     const bool wide = H.env[0].wpp == 2;  // the group shares its radii
     (void)wide;
+    uint32_t cen_items = 0;  // centralized-observation items this warp has copied out
     for (uint32_t c = 0; c <= n_chunks; ++c) {
         if (c >= 1) {
             const uint32_t cp = c - 1;
@@ -1302,22 +1349,28 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                 else
                     emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
             }
-            // the group is uniform in side, teams and radii
-            const bool row_central = P.central && !line_of_sight(H.env[0]);
-            if (row_central) {  // centralized observation, one thread per (step, env, row)
-                const uint32_t S = H.env[0].side, ne_ = (uint32_t)ne;
-                for (uint32_t it = (uint32_t)worker; it < C.len * ne_ * S; it += (uint32_t)n_workers) {
-                    const uint32_t ke = it / S, y = it - ke * S, k = ke / ne_, e = ke - k * ne_;
+            if (P.central) {  // centralized observation, one warp per (step, env)
+                const uint32_t S = H.env[0].side;  // uniform in the group
+                uint64_t* bufs = reinterpret_cast<uint64_t*>(sm + L.cen) + (warp - n_dyn) * 8 * S;
+                for (uint32_t it = (uint32_t)(warp - n_dyn); it < C.len * (uint32_t)ne; it += (uint32_t)M) {
+                    const uint32_t k = it / (uint32_t)ne, e = it - k * (uint32_t)ne;
                     const int first = L.first_slot[e];
                     const uint16_t* Tk = C.T + k * nsl + first;
                     const uint16_t* src = (Tk[0] & kDoneBit) ? H.p0 + first : Tk;
                     uint32_t sl = C.base_slot + k;
                     if (sl >= P.ring) sl -= P.ring;
-                    central_row(H.env[e], C.rows + L.rows_off[e], src, cell_shift(H.env[e]), (int)y,
-                                P.central + (uint64_t)sl * P.central_words + H.coff[e]);
+                    // two buffers in turn: the copy issued two items ago must have read this one
+                    uint64_t* buf = bufs + (cen_items & 1u) * 4 * S;
+                    if (cen_items >= 2) {
+                        if (lane == 0) bulk_wait_read1();
+                        __syncwarp();
+                    }
+                    central_warp(H.env[e], C.rows + L.rows_off[e], src, cell_shift(H.env[e]), lane, buf,
+                                 P.central + (uint64_t)sl * P.central_words + H.coff[e]);
+                    ++cen_items;
                 }
             }
-            if ((P.central && !row_central) || P.st_cells) {  // per (step, env)
+            if (P.st_cells) {  // per (step, env)
                 const uint32_t ne_ = (uint32_t)ne;
                 for (uint32_t it = (uint32_t)worker; it < C.len * ne_; it += (uint32_t)n_workers) {
                     const uint32_t k = it / ne_, e = it - k * ne_;
@@ -1328,15 +1381,11 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                     const uint32_t sh = cell_shift(E);
                     uint32_t sl = C.base_slot + k;
                     if (sl >= P.ring) sl -= P.ring;
-                    if (P.central && !row_central)
-                        central_env(E, C.rows + L.rows_off[e], src, sh,
-                                    P.central + (uint64_t)sl * P.central_words + H.coff[e]);
-                    if (P.st_cells) {  // the observed state: cells and the episode clock after the step
-                        uint16_t* cl = P.st_cells + (uint64_t)sl * P.agents + E.agent_off;
-                        for (int b = 0; b < E.n_agents; ++b) cl[b] = (uint16_t)to_hbm(src[b] & 0x0fffu, sh);
-                        P.st_ept[(uint64_t)sl * P.n_envs + H.gidx[e]] =
-                            (uint32_t)(((uint64_t)H.ept0[e] + C.k0 + k + 1u) % E.cap);
-                    }
+                    // the observed state: cells and the episode clock after the step
+                    uint16_t* cl = P.st_cells + (uint64_t)sl * P.agents + E.agent_off;
+                    for (int b = 0; b < E.n_agents; ++b) cl[b] = (uint16_t)to_hbm(src[b] & 0x0fffu, sh);
+                    P.st_ept[(uint64_t)sl * P.n_envs + H.gidx[e]] =
+                        (uint32_t)(((uint64_t)H.ept0[e] + C.k0 + k + 1u) % E.cap);
                 }
             }
             // Fog of war: one thread per fog row (env, unit, row y) scans the
@@ -1387,6 +1436,9 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
         if (c + 1 < n_chunks) draw_actions(c + 1, worker, n_workers);
         __syncthreads();
     }
+    // every bulk copy of this warp has completed (its shared source stays
+    // valid until then)
+    if (cen_items && lane == 0) bulk_wait_all();
     // the discovery rows for the next launch
     for (uint32_t u = (uint32_t)worker; u < fog_rows; u += (uint32_t)n_workers) {
         const int e = fog_env_of(u);
