@@ -114,9 +114,10 @@ def oracle_step(w, flags, unpacked):
         w.fog()
 
 
-def measured_traffic(workload_name):
-    """DRAM bytes per env-step of step_kernel from the committed ncu summary
-    of this workload, or None when the summary is missing or was taken on
+def measured_traffic(workload_name, key="traffic_bytes_per_env_step"):
+    """A per-env-step figure of step_kernel from the committed ncu summary of
+    this workload (DRAM bytes, or with key="warp_inst_per_env_step" issued
+    warp instructions), or None when the summary is missing or was taken on
     other kernel sources (the summary records their digest)."""
     from paper_2604_27162_gb300 import build as B
 
@@ -129,12 +130,12 @@ def measured_traffic(workload_name):
     vals = {}
     for line in text.splitlines():
         line = line.strip().strip("`")
-        if "=" in line and line.split("=", 1)[0] in ("traffic_bytes_per_env_step", "source_digest"):
-            key, val = line.split("=", 1)
-            vals[key] = val.strip()
-    if vals.get("source_digest") != B.source_digest() or "traffic_bytes_per_env_step" not in vals:
+        if "=" in line and line.split("=", 1)[0] in (key, "source_digest"):
+            name, val = line.split("=", 1)
+            vals[name] = val.strip()
+    if vals.get("source_digest") != B.source_digest() or key not in vals:
         return None
-    return float(vals["traffic_bytes_per_env_step"])
+    return float(vals[key])
 
 
 def peaks():
@@ -196,6 +197,19 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def issue_roofline(inst_per_env_step, env_steps_per_s, clk):
+    if inst_per_env_step is None or not clk or not clk.get("sm_mhz"):
+        return None
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = 4.0 * sms * clk["sm_mhz"] * 1e6
+    achieved = inst_per_env_step * env_steps_per_s
+    return {"achieved": achieved, "peak": peak, "unit": "warp-inst/s", "frac": achieved / peak,
+            "warp_inst_per_env_step": inst_per_env_step, "sms": sms,
+            "peak_kind": "4 warp instructions per cycle per SM at the sampled SM clock"}
 
 
 def workload(name):
@@ -331,6 +345,7 @@ def run_gpu(args):
     achieved = per_rank_bytes / (ms / 1e3) / 1e9
     peak, peak_kind = peaks()
     tpe = measured_traffic(args.workload) if args.mode == "default" else None
+    ipe = measured_traffic(args.workload, "warp_inst_per_env_step") if args.mode == "default" else None
     traffic = tpe * n_envs * run if tpe is not None else None  # bytes per launch
 
     # end to end through the public API: every step's results copied to
@@ -390,6 +405,10 @@ def run_gpu(args):
                 "algorithmic_bytes_per_launch": bpe * n_envs * run,
                 "traffic": traffic,
             },
+            # the SM instruction-issue view of the same kernel: ncu warp
+            # instructions per env-step x env-steps/s against 4 warp
+            # instructions per cycle per SM at the sampled SM clock
+            "issue": issue_roofline(ipe, value / world, clk),
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clk,
             "e2e": e2e,
