@@ -230,33 +230,36 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-// Wait until at most one copy group still reads its shared source.
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 // Wait until every copy group has completed.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // Order this thread's shared-memory writes before later bulk copies read them.
 __device__ __forceinline__ void fence_smem_to_bulk() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Centralized observation of one (step, env) by one warp (all lanes), built
-// in a buffer of 4 S words of shared memory laid out as the output block
-// ([4][S]: seen, seen obstacles, seen seekers, seen hiders).  Lane a (< A)
-// ORs its cell into the seeker or hider rows (words 2S.., 3S..) and, if its
-// team observes, its window rows (with line of sight: only the visible
-// cells, from one visibility mask) into the seen rows; then lane y turns
-// row y of each plane into its output value in place, and lane 0 copies the
-// block to global memory with one bulk copy (no generic stores, so the
-// warp's next __syncwarp does not wait for them).  The caller makes sure
-// the buffer is no longer read by an earlier copy.
-__device__ inline void central_warp(const EnvRT& E, const uint64_t* rows, const uint16_t* src, uint32_t sh,
-                                    int lane, uint64_t* buf, uint64_t* out) {
+// Wait until no copy group still reads its shared source.
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Centralized observation of one (step, env) by one half-warp (16 lanes;
+// the two halves of a warp build two blocks at once), in a buffer of 4 S
+// words of shared memory laid out as the output block ([4][S]: seen, seen
+// obstacles, seen seekers, seen hiders).  Lane a (< A <= 16) of the half ORs
+// its cell into the seeker or hider rows (words 2S.., 3S..) and, if its team
+// observes, its window rows (with line of sight: only the visible cells,
+// from one visibility mask) into the seen rows; then the half's lanes turn
+// rows into output values in place, 16 rows at a time, and its lane 0
+// copies the block to global memory with one bulk copy.  `live`: this half
+// has an item (the warp's barriers are taken by all 32 lanes either way).
+// The caller makes sure the buffer is no longer read by an earlier copy.
+__device__ inline void central_half(const EnvRT& E, const uint64_t* rows, const uint16_t* src, uint32_t sh,
+                                    int hl, bool live, uint64_t* buf, uint64_t* out) {
     const int S = E.side, A = E.n_agents, ns = E.n_seekers, rw = E.rw;
     const uint64_t smask = S == 64 ? ~0ull : ((1ull << S) - 1ull);
-    for (int y = lane; y < 4 * S; y += 32) buf[y] = 0ull;
+    if (live)
+        for (int y = hl; y < 4 * S; y += 16) buf[y] = 0ull;
     __syncwarp();
-    if (lane < A) {
-        const uint32_t v = src[lane] & 0x0fffu;
+    if (live && hl < A) {
+        const uint32_t v = src[hl] & 0x0fffu;
         const int xa = (int)(v & ((1u << sh) - 1u)), ya = (int)(v >> sh);
-        const int team = lane < ns ? 0 : 1;
+        const int team = hl < ns ? 0 : 1;
         const bool wide = S > 32;
         or_row(buf + (team ? 3 * S : 2 * S) + ya, 1ull << xa, wide);
         if (team_sees(E, team)) {
@@ -280,18 +283,20 @@ __device__ inline void central_warp(const EnvRT& E, const uint64_t* rows, const 
         }
     }
     __syncwarp();
-    for (int y = lane; y < S; y += 32) {  // each lane reads, then rewrites, only row y
-        const uint64_t seen = buf[y];
-        const uint64_t* pr = rows + (y + kPad) * rw;
-        const uint64_t obst = (rw == 1 ? (pr[0] >> kPad) : ((pr[0] >> kPad) | (pr[1] << (64 - kPad)))) & smask;
-        const uint64_t sk = buf[2 * S + y], hd = buf[3 * S + y];
-        buf[S + y] = seen & obst;
-        buf[2 * S + y] = seen & sk;
-        buf[3 * S + y] = seen & hd;
+    if (live) {
+        for (int y = hl; y < S; y += 16) {  // each lane reads, then rewrites, only its rows
+            const uint64_t seen = buf[y];
+            const uint64_t* pr = rows + (y + kPad) * rw;
+            const uint64_t obst = (rw == 1 ? (pr[0] >> kPad) : ((pr[0] >> kPad) | (pr[1] << (64 - kPad)))) & smask;
+            const uint64_t sk = buf[2 * S + y], hd = buf[3 * S + y];
+            buf[S + y] = seen & obst;
+            buf[2 * S + y] = seen & sk;
+            buf[3 * S + y] = seen & hd;
+        }
+        fence_smem_to_bulk();
     }
-    fence_smem_to_bulk();
     __syncwarp();
-    if (lane == 0) bulk_store(out, buf, 32u * (uint32_t)S);
+    if (live && hl == 0) bulk_store(out, buf, 32u * (uint32_t)S);
 }
 
 // Row y of the cells seen by agents a0..a1-1 of an env without line of
@@ -1349,23 +1354,24 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                 else
                     emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
             }
-            if (P.central) {  // centralized observation, one warp per (step, env)
+            if (P.central) {  // centralized observation, two (step, env) items per warp
                 const uint32_t S = H.env[0].side;  // uniform in the group
-                uint64_t* bufs = reinterpret_cast<uint64_t*>(sm + L.cen) + (warp - n_dyn) * 8 * S;
-                for (uint32_t it = (uint32_t)(warp - n_dyn); it < C.len * (uint32_t)ne; it += (uint32_t)M) {
-                    const uint32_t k = it / (uint32_t)ne, e = it - k * (uint32_t)ne;
+                const int half = lane >> 4, hl = lane & 15;
+                uint64_t* buf = reinterpret_cast<uint64_t*>(sm + L.cen) + ((warp - n_dyn) * 2 + half) * 4 * S;
+                const uint32_t n_items = C.len * (uint32_t)ne;
+                for (uint32_t it0 = 2u * (uint32_t)(warp - n_dyn); it0 < n_items; it0 += 2u * (uint32_t)M) {
+                    const uint32_t it = it0 + (uint32_t)half;
+                    const bool live = it < n_items;
+                    const uint32_t k = live ? it / (uint32_t)ne : 0u, e = live ? it - k * (uint32_t)ne : 0u;
                     const int first = L.first_slot[e];
                     const uint16_t* Tk = C.T + k * nsl + first;
                     const uint16_t* src = (Tk[0] & kDoneBit) ? H.p0 + first : Tk;
                     uint32_t sl = C.base_slot + k;
                     if (sl >= P.ring) sl -= P.ring;
-                    // two buffers in turn: the copy issued two items ago must have read this one
-                    uint64_t* buf = bufs + (cen_items & 1u) * 4 * S;
-                    if (cen_items >= 2) {
-                        if (lane == 0) bulk_wait_read1();
-                        __syncwarp();
-                    }
-                    central_warp(H.env[e], C.rows + L.rows_off[e], src, cell_shift(H.env[e]), lane, buf,
+                    // the half's previous copy must have read the buffer
+                    if (cen_items && hl == 0) bulk_wait_read0();
+                    __syncwarp();
+                    central_half(H.env[e], C.rows + L.rows_off[e], src, cell_shift(H.env[e]), hl, live, buf,
                                  P.central + (uint64_t)sl * P.central_words + H.coff[e]);
                     ++cen_items;
                 }
@@ -1437,8 +1443,8 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
         __syncthreads();
     }
     // every bulk copy of this warp has completed (its shared source stays
-    // valid until then)
-    if (cen_items && lane == 0) bulk_wait_all();
+    // valid until then); lanes 0 and 16 issued them
+    if (cen_items && (lane & 15) == 0) bulk_wait_all();
     // the discovery rows for the next launch
     for (uint32_t u = (uint32_t)worker; u < fog_rows; u += (uint32_t)n_workers) {
         const int e = fog_env_of(u);
