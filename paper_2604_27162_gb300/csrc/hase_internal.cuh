@@ -110,6 +110,7 @@ struct GroupPlan {
     uint32_t n_dyn;
     uint32_t n_envs;
     uint32_t n_slots;
+    uint32_t max_side;                   // largest grid side of the group (sides may differ)
     uint32_t act_words;                  // uint32 words per action buffer
     uint32_t act, traj, rows, claim, tbl, state, fog, cen, total;  // byte offsets
     uint16_t flags;
@@ -151,7 +152,7 @@ __host__ __device__ inline uint32_t fog_units(const EnvRT& E, bool per_agent) {
 // group does not fit the dynamics warps.
 __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uint16_t flags,
                                            GroupPlan& G) {
-    uint32_t ro = 0, co = 0, to = 0, fo = 0, slot = 0;
+    uint32_t ro = 0, co = 0, to = 0, fo = 0, slot = 0, max_side = 0;
     int dyn = 0;
     uint32_t dyn_slots = 0;
     G.dyn_first[0] = 0;
@@ -166,6 +167,7 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
         dyn_slots += E.n_agents;
         G.first_slot[i] = (uint8_t)slot;
         slot += E.n_agents;
+        max_side = E.side > max_side ? E.side : max_side;
         G.rows_off[i] = ro;
         ro += (uint32_t)(E.side + 2 * kPad) * E.rw;
         G.cell_off[i] = co;
@@ -187,6 +189,7 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
     G.fog_off[n] = fo;
     G.n_dyn = (uint32_t)dyn + 1;
     G.n_envs = (uint32_t)n;
+    G.max_side = max_side;
     G.n_slots = slot;
     G.dyn_first[dyn + 1] = (uint8_t)slot;
     const uint32_t ns = slot, kcu = (uint32_t)kc;
@@ -199,7 +202,7 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
     G.state = G.tbl + to * 8;                            // uint8 per cell
     G.fog = align_up(G.state + co, 16);                  // uint64 per fog row
     G.cen = align_up(G.fog + fo * 8, 16);                // uint64 [emit warps][2][4][side]
-    const uint32_t cen_words = (flags & kCentral) && n ? kMaxEmitWarps * 8u * envs[0].side : 0u;
+    const uint32_t cen_words = (flags & kCentral) ? kMaxEmitWarps * 8u * max_side : 0u;
     G.total = align_up(G.cen + cen_words * 8, 16);
     G.flags = flags;
     return true;

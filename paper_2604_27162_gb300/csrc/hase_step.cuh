@@ -1379,7 +1379,9 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                     emit_chunk<2>(P, H, C, warp - n_dyn, M, lane);
             }
             if (P.central) {  // centralized observation, two (step, env) items per warp
-                const uint32_t S = H.env[0].side;  // uniform in the group
+                // block buffers of the group's largest side (envs of a group
+                // share their packing, not necessarily their side)
+                const uint32_t S = L.max_side;
                 const int half = lane >> 4, hl = lane & 15;
                 uint64_t* buf = reinterpret_cast<uint64_t*>(sm + L.cen) + ((warp - n_dyn) * 2 + half) * 4 * S;
                 const uint32_t n_items = C.len * (uint32_t)ne;

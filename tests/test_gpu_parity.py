@@ -239,6 +239,19 @@ def test_optional_exports_edge_cases(desc, flags):
     compare_run(9, 77, [desc], 40, flags=flags | hase.HASE_EXPORT_ACTIONS, launches=[1, 17, 22], chunk_steps=8)
 
 
+@pytest.mark.parametrize("teams", [3, 3 | 4], ids=["plain", "los"])
+def test_mixed_sides_in_one_cta(teams):
+    """Envs of one kernel shape but different sides share a CTA (the shape key
+    holds the cell packing, not the side): every export must size its
+    per-CTA buffers for the largest side."""
+    descs = [W.env_desc(side, 6, 3, 2, 2, 30, "0.2", teams) for side in (8, 16, 24, 32, 12, 20)] * 4
+    flags = (hase.HASE_EXPORT_CENTRAL | hase.HASE_EXPORT_FOG | hase.HASE_EXPORT_STATE
+             | hase.HASE_EXPORT_ACTIONS)
+    compare_run(24, 52, descs, 70, flags=flags, max_group_envs=6, launches=[33, 37])
+    compare_run(24, 53, descs, 40, flags=flags | hase.HASE_FOG_PER_AGENT | hase.HASE_SKIP_OBS,
+                max_group_envs=6)
+
+
 def test_ring_wraparound_and_split_launches():
     c = W.ten1k()
     compare_run(64, c["seed"], c["descs"], 300, ring=7, launches=[1, 2, 97, 200])
