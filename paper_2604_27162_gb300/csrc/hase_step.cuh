@@ -1,11 +1,12 @@
 // hase_step.cuh -- device code of the fused step kernel (a1-a9), included
 // by one translation unit per kernel family (hase_step_f0.cu ..
-// hase_step_f4.cu, compiled in parallel) and by hase_kernels.cu for the
+// hase_step_f12.cu, compiled in parallel) and by hase_kernels.cu for the
 // shared helpers.
 //
 //   step_kernel     a1-a9 fused over K steps.  One CTA owns a group of envs
-//                   of identical shape for the whole launch, all dynamic
-//                   state in shared memory and registers:
+//                   of one kernel shape (agents, teams, radii, cell packing)
+//                   for the whole launch, all dynamic state in shared memory
+//                   and registers:
 //                     dynamics warps (a2, a3, a7, a8): one lane per agent
 //                       slot, whole envs per warp; a mover writes its lane
 //                       into the claim byte of its incoming direction in the
@@ -16,9 +17,11 @@
 //                     emission warps (a1, a4-a6, a9), one chunk behind:
 //                       one thread per (step, env) builds every agent's
 //                       three planes with packed-byte window tests (one lane
-//                       per agent for windows over 64 bits), the rewards and
-//                       the done byte, stores them, and draws the Philox
-//                       actions of the next chunk.
+//                       per agent for the shapes outside the families
+//                       1-12), the rewards and the done byte, stores them,
+//                       writes the optional exports (centralized
+//                       observation, true state, fog of war), and draws the
+//                       Philox actions of the next chunk.
 #pragma once
 
 #include <cuda_runtime.h>
