@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libhase.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["hase_step_f%d.cu" % f for f in range(13)] + ["hase_kernels.cu", "hase_api.cu", "hase_serve.cu"]
+SOURCES = ["hase_step_f%d.cu" % f for f in range(17)] + ["hase_kernels.cu", "hase_api.cu", "hase_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]

@@ -233,7 +233,7 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
         const int fam0 = family_of(genv[0]);
         if (plan.total <= h->smem_budget) {
             flags |= kUseTable;
-        } else if (fam0 >= 9) {  // line-of-sight families: one table for both radii
+        } else if (fam0 >= 9 && fam0 <= 12) {  // one-word line-of-sight families: one table for both radii
             plan_group(genv.data(), g.n_envs, (int)h->kc, flags | kUseTable | kSharedTable, plan);
             if (plan.total <= h->smem_budget) flags |= kUseTable | kSharedTable;
         }

@@ -117,22 +117,22 @@ struct GroupPlan {
 };
 
 // One thread emits a whole (step, env) when the seekers are the first
-// ceil(A / 2) agents (windows of up to two words a plane; with line of
-// sight, of one word); other shapes take the lane-per-agent emission.
+// ceil(A / 2) agents (windows of up to two words a plane); other shapes take
+// the lane-per-agent emission.
 __host__ __device__ inline bool fast_emission(const EnvRT& E) {
-    return E.wpp <= 2 && E.n_seekers == (E.n_agents + 1u) / 2u && (!(E.obs_teams & kObsLos) || E.wpp <= 1);
+    return E.wpp <= 2 && E.n_seekers == (E.n_agents + 1u) / 2u;
 }
 
 // Kernel families: family 0 runs the general (lane per agent) emission;
 // families 1..4 the one-thread emission for A in 1-4, 5-8, 9-12, 13-16 with
 // one word a plane, families 5..8 the same with two words a plane (radius 4),
-// families 9..12 the one-word forms with line of sight.  Each group is
-// launched with the kernel of its family.
-constexpr int kFamilies = 13;
+// families 9..12 and 13..16 the one- and two-word forms with line of sight.
+// Each group is launched with the kernel of its family.
+constexpr int kFamilies = 17;
 __host__ __device__ inline int family_of(const EnvRT& E) {
     if (!fast_emission(E)) return 0;
-    if (E.obs_teams & kObsLos) return 9 + ((int)E.n_agents - 1) / 4;
-    return (E.wpp == 2 ? 5 : 1) + ((int)E.n_agents - 1) / 4;
+    const int base = (E.obs_teams & kObsLos) ? (E.wpp == 2 ? 13 : 9) : (E.wpp == 2 ? 5 : 1);
+    return base + ((int)E.n_agents - 1) / 4;
 }
 
 // Radius of the shared window table: the larger emitting radius.

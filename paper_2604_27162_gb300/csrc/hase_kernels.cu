@@ -382,6 +382,10 @@ HASE_FAMILY_DECL(9)
 HASE_FAMILY_DECL(10)
 HASE_FAMILY_DECL(11)
 HASE_FAMILY_DECL(12)
+HASE_FAMILY_DECL(13)
+HASE_FAMILY_DECL(14)
+HASE_FAMILY_DECL(15)
+HASE_FAMILY_DECL(16)
 #undef HASE_FAMILY_DECL
 
 // Opt in, once per device and outside any capture, to all the dynamic shared
@@ -398,7 +402,8 @@ cudaError_t prepare_step(uint32_t smem) {
     if (e != cudaSuccess) return e;
     if ((int)smem + 8 * 1024 > optin) return cudaErrorInvalidValue;
     cudaError_t (*opt[])(int) = {opt_in_f0, opt_in_f1, opt_in_f2,  opt_in_f3,  opt_in_f4,  opt_in_f5, opt_in_f6,
-                                 opt_in_f7, opt_in_f8, opt_in_f9, opt_in_f10, opt_in_f11, opt_in_f12};
+                                 opt_in_f7, opt_in_f8, opt_in_f9, opt_in_f10, opt_in_f11, opt_in_f12,
+                                 opt_in_f13, opt_in_f14, opt_in_f15, opt_in_f16};
     for (auto f : opt)
         if ((e = f(optin)) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = 1;
@@ -423,6 +428,10 @@ cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint
         case 10: return launch_f10(p, n_groups, threads, smem, st);
         case 11: return launch_f11(p, n_groups, threads, smem, st);
         case 12: return launch_f12(p, n_groups, threads, smem, st);
+        case 13: return launch_f13(p, n_groups, threads, smem, st);
+        case 14: return launch_f14(p, n_groups, threads, smem, st);
+        case 15: return launch_f15(p, n_groups, threads, smem, st);
+        case 16: return launch_f16(p, n_groups, threads, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }

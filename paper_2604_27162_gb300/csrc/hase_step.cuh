@@ -1,6 +1,6 @@
 // hase_step.cuh -- device code of the fused step kernel (a1-a9), included
 // by one translation unit per kernel family (hase_step_f0.cu ..
-// hase_step_f12.cu, compiled in parallel) and by hase_kernels.cu for the
+// hase_step_f16.cu, compiled in parallel) and by hase_kernels.cu for the
 // shared helpers.
 //
 //   step_kernel     a1-a9 fused over K steps.  One CTA owns a group of envs
@@ -18,7 +18,7 @@
 //                       one thread per (step, env) builds every agent's
 //                       three planes with packed-byte window tests (one lane
 //                       per agent for the shapes outside the families
-//                       1-12), the rewards and the done byte, stores them,
+//                       1-16), the rewards and the done byte, stores them,
 //                       writes the optional exports (centralized
 //                       observation, true state, fog of war), and draws the
 //                       Philox actions of the next chunk.
@@ -811,11 +811,16 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
     w.o0h = 0;
     {  // a5 obstacle plane (and, with line of sight, the visible cells)
         uint64_t vis = ~0ull;
+        uint32_t vis_hi = ~0u;  // bits 64-80 of two-word windows
         if (T.use_table) {
-            if (W2 && R == 4u) {  // two table words a cell
-                const uint64_t* c = T.tbl + 2u * (ya * T.side + xa);
+            if (W2 && R == 4u) {  // two table words a cell (four with line of sight)
+                const uint64_t* c = T.tbl + (LOS ? 4u : 2u) * (ya * T.side + xa);
                 w.o0 = c[0];
                 w.o0h = (uint32_t)c[1];
+                if (LOS) {
+                    vis = c[2];
+                    vis_hi = (uint32_t)c[3];
+                }
             } else if (LOS) {  // one-word windows: obstacle plane, then visibility
                 const uint64_t* c = T.tbl + 2u * (ya * T.side + xa);
                 w.o0 = c[0];
@@ -834,12 +839,18 @@ __device__ __forceinline__ Words3 observer_words(const TeamCtx& T, int a, uint32
             if (LOS) {
                 uint64_t vh;
                 window_visibility(w.o0, hi, (int)R, vis, vh);
+                vis_hi = (uint32_t)vh;
             }
         }
-        if (LOS) {  // hidden cells read 0 in all three planes (one-word windows)
+        if (LOS) {  // hidden cells read 0 in all three planes
             w.o0 &= vis;
             w.al &= vis;
             w.op &= vis;
+            if (W2) {
+                w.o0h &= vis_hi;
+                w.alh &= vis_hi;
+                w.oph &= vis_hi;
+            }
         }
         if (T.unp) {
             if (W2)
@@ -1047,8 +1058,8 @@ template <int FAM>
 __device__ __forceinline__ void emit_fast_dispatch(int A, const StepParams& P, const CtaShared& H,
                                                    const EmitCtx& C) {
     constexpr int a0 = 4 * ((FAM - 1) % 4) + 1;
-    constexpr bool W2 = FAM >= 5 && FAM <= 8;  // two words a plane
-    constexpr bool LOS = FAM >= 9;             // line of sight, one word a plane
+    constexpr bool W2 = (FAM >= 5 && FAM <= 8) || FAM >= 13;  // two words a plane
+    constexpr bool LOS = FAM >= 9;                             // line of sight
     if (A == a0) emit_segments_fast<a0, W2, LOS>(P, H, C);
     else if (A == a0 + 1) emit_segments_fast<a0 + 1, W2, LOS>(P, H, C);
     else if (A == a0 + 2) emit_segments_fast<a0 + 2, W2, LOS>(P, H, C);

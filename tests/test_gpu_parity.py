@@ -110,6 +110,8 @@ def test_desynchronised_start_matches_oracle():
     W.env_desc(12, 5, 3, 2, 2, 30, "0.2", 2 | 4),      # hiders only emit
     W.env_desc(10, 3, 2, 2, 3, 30, "0.2", 1 | 4),      # one-thread emission, 1-4 agents
     W.env_desc(20, 16, 8, 3, 1, 30, "0.25", 3 | 4),    # one-thread emission, 13-16 agents
+    W.env_desc(12, 3, 2, 4, 4, 30, "0.2", 1 | 4),      # two-word windows, 1-4 agents
+    W.env_desc(20, 16, 8, 4, 2, 30, "0.25", 3 | 4),    # two-word windows, 13-16 agents
 ])
 def test_line_of_sight_matches_oracle(desc):
     compare_run(36, 17, [desc], 70, flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED)
