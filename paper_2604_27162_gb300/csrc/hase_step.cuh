@@ -325,19 +325,20 @@ __device__ __forceinline__ RowSeen row_seen_ctx(const EnvRT& E) {
     c.h_sees = team_sees(E, 1);
     return c;
 }
-// The same for four steps at once (four independent chains for the
-// scheduler): src[j] holds step j's cells.
-__device__ __forceinline__ void row_seen4(const RowSeen& c, const uint16_t* const (&src)[4], int a0, int a1, int y,
-                                          uint64_t (&seen)[4]) {
+// The same for N steps at once (N independent chains for the scheduler):
+// src[j] holds step j's cells.
+template <int N>
+__device__ __forceinline__ void row_seen_n(const RowSeen& c, const uint16_t* const (&src)[N], int a0, int a1, int y,
+                                           uint64_t (&seen)[N]) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) seen[j] = 0ull;
+    for (int j = 0; j < N; ++j) seen[j] = 0ull;
     for (int a = a0; a < a1; ++a) {
         const bool hider = a >= c.ns;
         if (!(hider ? c.h_sees : c.s_sees)) continue;
         const int R = hider ? c.rh : c.rs;
         const uint64_t w = hider ? c.wh : c.ws;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < N; ++j) {
             const uint32_t v = src[j][a] & 0x0fffu;
             const int x0 = (int)(v & c.xmask) - R;
             const bool in = (uint32_t)(y - (int)(v >> c.sh) + R) <= (uint32_t)(2 * R);
@@ -346,7 +347,7 @@ __device__ __forceinline__ void row_seen4(const RowSeen& c, const uint16_t* cons
         }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) seen[j] &= c.smask;
+    for (int j = 0; j < N; ++j) seen[j] &= c.smask;
 }
 
 __device__ __forceinline__ uint64_t row_seen(const RowSeen& c, const uint16_t* src, int a0, int a1, int y) {
@@ -1454,20 +1455,21 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                     uint64_t disc = s_fog[u];
                     uint32_t sl = C.base_slot;
                     uint32_t k = 0;
-                    if (!los) {  // four steps' rows at a time, then the scan in step order
-                        for (; k + 4 <= C.len; k += 4) {
-                            const uint16_t* src[4];
-                            bool done[4];
+                    if (!los) {  // several steps' rows at a time, then the scan in step order
+                        constexpr int NB = FAM == 0 ? 4 : 8;  // family 0 runs at 128 registers
+                        for (; k + NB <= C.len; k += NB) {
+                            const uint16_t* src[NB];
+                            bool done[NB];
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
+                            for (int j = 0; j < NB; ++j) {
                                 const uint16_t* Tk = C.T + (k + j) * nsl + first;
                                 done[j] = (Tk[0] & kDoneBit) != 0u;
                                 src[j] = done[j] ? H.p0 + first : Tk;
                             }
-                            uint64_t seen[4];
-                            row_seen4(rs, src, a0, a1, (int)y, seen);
+                            uint64_t seen[NB];
+                            row_seen_n<NB>(rs, src, a0, a1, (int)y, seen);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
+                            for (int j = 0; j < NB; ++j) {
                                 const uint64_t prev = done[j] ? 0ull : disc;
                                 disc = prev | seen[j];
                                 uint64_t* o = out + (uint64_t)sl * P.fog_words;
