@@ -151,6 +151,63 @@ def _generation(L):
     return abs(both / pairs - q) < 4 * (q * (1 - q) / pairs) ** 0.5
 
 
+def _keying(L):
+    """Start cells and obstacles recomputed from the Philox block (itself
+    pinned against ATen's engine): start cell of agent a = floor(u S^2 / 2^32)
+    with u = word 0 of counter (attempt, a, env, 2), row-major (x = cell mod S,
+    y = cell div S), redrawn while taken; cell c is an obstacle iff word c mod 4
+    of counter (c div 4, 0, env, 1) is below the threshold, start cells free.
+    Odd sides and a nonzero env-id base make a transposed or shifted index
+    visible."""
+    for S, A, dens, seed, base in ((13, 5, "0.3", 11, 0), (32, 10, "0.2", 2, 1000),
+                                   (7, 3, "0.5", (1 << 40) + 3, 77)):
+        d = W.env_desc(S, A, (A + 1) // 2, 2, 2, 50, dens)
+        n = 3
+        w = oracle.World(n, seed, [d], env_id_base=base, L=L)
+        st = w.state()
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        for e in range(n):
+            env = base + e
+            cells = []
+            for a in range(A):
+                att = 0
+                while True:
+                    u = int(oracle.philox4x32_10((att, a, env, 2), key, L=L)[0])
+                    c = (u * S * S) >> 32
+                    if c not in cells:
+                        break
+                    att += 1
+                cells.append(c)
+            sl = slice(e * A, (e + 1) * A)
+            if [int(v) for v in st["sx"][sl]] != [c % S for c in cells]:
+                return False
+            if [int(v) for v in st["sy"][sl]] != [c // S for c in cells]:
+                return False
+            g = w.grid(e)
+            for c in range(S * S):
+                u = int(oracle.philox4x32_10((c >> 2, 0, env, 1), key, L=L)[c & 3])
+                if int(g[c // S, c % S]) != (0 if c in cells else int(u < d["density_thr"])):
+                    return False
+    return True
+
+
+def splitmix64_known_answers():
+    """(state before the output, expected output) pairs of the published
+    splitmix64 sequence from state 0 (tests/golden/splitmix64_seed0.txt)."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64_seed0.txt")
+    vals = [int(ln, 16) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    gamma = 0x9E3779B97F4A7C15
+    return [((k * gamma) & ((1 << 64) - 1), v) for k, v in enumerate(vals)]
+
+
+def _digest(L):
+    """The digest's mixing function against the published splitmix64
+    outputs (the oracle's ho_splitmix64 adds the gamma itself)."""
+    return all(oracle.splitmix64(z, L=L) == v for z, v in splitmix64_known_answers())
+
+
 def _run(L):
     desc = dict(W.ten1k()["descs"][0], cap=20)
     n = 6
@@ -285,6 +342,8 @@ CHECKS = {
     "rewards": _rewards,
     "observations": _observations,
     "generation": _generation,
+    "keying": _keying,
+    "digest": _digest,
     "run": _run,
     "modes": _modes,
 }

@@ -1,7 +1,7 @@
 """Mutation test of the oracle's pins (CPU only).
 
 Each mutant plants one plausible mistake in a copy of the oracle's C source
-(a dropped term, a wrong sign or index, a transposed operand), builds it with
+(a dropped term, a wrong sign or index, a transposed operand; a few need two edits to stay consistent), builds it with
 gcc in a temporary directory and runs the pin battery against it in a child
 process.  Every mutant must fail at least one pin; the unmodified oracle must
 pass them all.  The mistakes are planted in the oracle, on the CPU only.
@@ -64,7 +64,23 @@ MUTANTS = [
     ("fog not updated on steps", "    if (w->fog) fog_env(w, e, d != 0);\n", "\n"),
     ("true state x and y transposed", "cells[i] = (uint16_t)((uint32_t)w->x[i] | ((uint32_t)w->y[i] << 6));",
      "cells[i] = (uint16_t)((uint32_t)w->y[i] | ((uint32_t)w->x[i] << 6));"),
+    # a consistent transposition: agents start at (cell / S, cell % S) and
+    # that cell is the one forced free, so every invariant still holds
+    ("start x and y transposed", [
+        ("w->sx[base + a] = (int32_t)(cells[a] % S);\n        w->sy[base + a] = (int32_t)(cells[a] / S);",
+         "w->sx[base + a] = (int32_t)(cells[a] / S);\n        w->sy[base + a] = (int32_t)(cells[a] % S);"),
+        ("for (uint32_t a = 0; a < p->n_agents; ++a) g[cells[a]] = 0;",
+         "for (uint32_t a = 0; a < p->n_agents; ++a) g[(cells[a] % S) * S + cells[a] / S] = 0;")]),
+    ("obstacle counter c instead of c / 4", "philox_words(w->seed, c / 4u, 0u, env_id, 1u, out);",
+     "philox_words(w->seed, c, 0u, env_id, 1u, out);"),
+    ("splitmix64 first shift", "z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;",
+     "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;"),
 ]
+
+
+def _edits(m):
+    """(old, new) replacements of a mutant: one pair, or a list of pairs."""
+    return m[1] if isinstance(m[1], list) else [(m[1], m[2])]
 
 
 @pytest.fixture(scope="module")
@@ -104,10 +120,13 @@ def test_unmodified_oracle_passes_battery(tmp_path, aten_driver):
     assert _battery(so, aten_driver) == []
 
 
-@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_mutant_is_caught(name, old, new, tmp_path, aten_driver):
+@pytest.mark.parametrize("mutant", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(mutant, tmp_path, aten_driver):
+    name = mutant[0]
     text = open(SRC).read()
-    assert text.count(old) == 1, name
-    so = _build(text.replace(old, new), tmp_path)
+    for old, new in _edits(mutant):
+        assert text.count(old) == 1, name
+        text = text.replace(old, new)
+    so = _build(text, tmp_path)
     failed = _battery(so, aten_driver)
     assert failed, "mutant not caught: " + name

@@ -452,6 +452,27 @@ def test_digest_matches_step_outputs():
     assert res["digest"] == dig
 
 
+def test_splitmix64_known_answers():
+    """The digest's mixing function reproduces the published splitmix64
+    output sequence from state 0 (Steele, Lea, Flood 2014; the values in
+    tests/golden/splitmix64_seed0.txt come with the reference implementation,
+    not from this code)."""
+    from tests.pin_battery import splitmix64_known_answers
+
+    ka = splitmix64_known_answers()
+    assert len(ka) == 5
+    for z, v in ka:
+        assert oracle.splitmix64(z) == v, (hex(z), hex(v))
+
+
+def test_start_cells_and_obstacles_follow_keying():
+    """Start cells and obstacles of worlds with odd sides and nonzero env-id
+    bases, recomputed from the Philox block pinned against ATen."""
+    from tests.pin_battery import _keying
+
+    assert _keying(oracle.lib())
+
+
 def test_invalid_params_rejected():
     with pytest.raises(ValueError):
         oracle.World(2, 0, [W.env_desc(0, 1, 1, 1, 1, 5, 0)])
