@@ -259,7 +259,9 @@ def build_form(form, c, run, flags, stream, base, log):
     setting = {}
     if form == "batched":
         t = time.perf_counter()
-        setting, trials = autotune.tune(n_envs, c["seed"], c["descs"], flags, stream=stream, log=log)
+        knobs = [(k, v) for k, v in autotune.KNOBS if k != "step_form" or not flags & (
+            H.HASE_CHUNKED_STEP | H.HASE_STREAM_STEP)]  # a form given on the command line is kept
+        setting, trials = autotune.tune(n_envs, c["seed"], c["descs"], flags, stream=stream, log=log, knobs=knobs)
         extra["autotune"] = {"setting": setting, "trials": len(trials),
                              "seconds": round(time.perf_counter() - t, 1)}
     eng = hase.Engine(n_envs, c["seed"], c["descs"], ring_steps=run, flags=flags, env_id_base=base,
@@ -305,6 +307,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     hase.load()
     c, flags = apply_mode(workload(args.workload), args.mode)
+    flags |= H.STEP_FORMS[args.step_form]
     n_envs = c["n_envs"]
     run = args.run_steps or RUN_STEPS[args.workload]
     # weak scaling: rank r steps envs [r*E, (r+1)*E) of the global batch
@@ -381,6 +384,7 @@ def run_gpu(args):
             "config": {
                 "workload": args.workload,
                 "mode": args.mode,
+                "step_form": args.step_form,
                 "flags": flags,
                 "n_envs_per_gpu": n_envs,
                 "env_steps_per_bench_step": run,
@@ -708,6 +712,9 @@ def main():
     ap.add_argument("--streams", type=int, default=16, help="served: CUDA streams of the server")
     ap.add_argument("--serial-seconds", type=float, default=5.0,
                     help="served: seconds of the stream also served one request at a time")
+    ap.add_argument("--step-form", choices=sorted(H.STEP_FORMS), default="auto",
+                    help="step kernel form: auto (the engine's choice; the batched form lets the autotuner "
+                         "choose), chunked or stream")
     ap.add_argument("--no-compare", action="store_true",
                     help="batched form: skip timing the plain and per-config forms beside it")
     args = ap.parse_args()

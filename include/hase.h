@@ -126,6 +126,18 @@ typedef enum hase_status {
                                 /* column x): discovered, newly discovered   */
                                 /* in this step.  A reset starts a new map.  */
 #define HASE_FOG_PER_AGENT 512u /* one fog unit per observing agent          */
+#define HASE_CHUNKED_STEP 1024u /* step kernel forms (identical outputs):    */
+#define HASE_STREAM_STEP 2048u  /* chunked -- all warps of a CTA meet at a   */
+                                /* barrier every chunk of steps -- or        */
+                                /* streaming -- the dynamics write an on-chip */
+                                /* trajectory ring that the output warps read */
+                                /* behind progress counters.  The streaming  */
+                                /* form applies to seekers = ceil(A/2), no   */
+                                /* line of sight, no HASE_EXPORT_CENTRAL or  */
+                                /* HASE_EXPORT_FOG, ring_steps >= 160; by    */
+                                /* default it runs when the batch needs more */
+                                /* CTAs than the GPU has SMs.  These flags   */
+                                /* force one form (not both)                 */
 #define HASE_POOL_ALLOC 8u      /* buffers from the device's stream-ordered  */
                                 /* pool (allocated on the create stream,     */
                                 /* returned by hase_destroy on the stream of */

@@ -1,10 +1,10 @@
 """Launch-configuration autotuner of the batched step.
 
-The knobs are the ones `hase_create` takes: the shared-memory cap of a CTA
-(which decides how many envs share a CTA and whether the per-cell window
-tables fit, hence how many CTAs an SM holds), the emission warps per CTA, the
-envs packed per CTA, the steps per on-chip chunk and the steps fused per
-launch.  Each candidate is measured on a short rollout of the actual batch,
+The knobs are the ones `hase_create` takes: the form of the step kernel
+(chunked or streaming), the shared-memory cap of a CTA (which decides how
+many envs share a CTA and whether the per-cell window tables fit, hence how
+many CTAs an SM holds), the emission warps per CTA, the envs packed per CTA,
+the steps per on-chip chunk and the steps fused per launch.  Each candidate is measured on a short rollout of the actual batch,
 replayed as a CUDA graph exactly as the timed run will be, and the fastest
 is kept.  The search is coordinate descent from the engine's own defaults:
 one knob at a time, keeping the best value before moving to the next.
@@ -16,6 +16,7 @@ import time
 from . import hase
 
 KNOBS = [
+    ("step_form", ["auto", "chunked", "stream"]),
     ("smem_cap", [0, 49152, 65536, 98304, 131072, 163840]),
     ("emit_warps", [0, 3, 4, 6, 8]),
     ("max_group_envs", [0, 1, 2, 4]),
@@ -29,7 +30,7 @@ def measure(n_envs, seed, descs, flags, setting, probe_steps, repeats=3, stream=
     import torch
 
     try:
-        eng = hase.Engine(n_envs, seed, descs, ring_steps=probe_steps, flags=flags, stream=stream,
+        eng = hase.Engine(n_envs, seed, descs, ring_steps=max(probe_steps, 160), flags=flags, stream=stream,
                           **{k: v for k, v in setting.items() if v})
     except hase.HaseError:
         return None
@@ -52,7 +53,7 @@ def measure(n_envs, seed, descs, flags, setting, probe_steps, repeats=3, stream=
 def tune(n_envs, seed, descs, flags=0, probe_steps=128, knobs=None, stream=None, log=None):
     """Returns (best setting, list of (setting, seconds)) for the batch."""
     knobs = knobs or KNOBS
-    best = {k: 0 for k, _ in knobs}
+    best = {k: vals[0] for k, vals in knobs}
     best_s = measure(n_envs, seed, descs, flags, best, probe_steps, stream=stream)
     if best_s is None:
         raise RuntimeError("the default launch configuration cannot be built")
@@ -74,4 +75,4 @@ def tune(n_envs, seed, descs, flags=0, probe_steps=128, knobs=None, stream=None,
     if log:
         log("autotune: best %s (%.3f ms per %d steps) after %d trials, %.1f s"
             % (best, best_s * 1e3, probe_steps, len(trials), time.perf_counter() - t_start))
-    return {k: v for k, v in best.items() if v}, trials
+    return {k: v for k, v in best.items() if v and v != "auto"}, trials

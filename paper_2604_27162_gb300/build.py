@@ -15,7 +15,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libhase.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["hase_step_f%d.cu" % f for f in range(17)] + ["hase_kernels.cu", "hase_api.cu", "hase_serve.cu"]
+# (source, object, extra flags): the step kernel's family source once per family
+FAMILIES = 17
+UNITS = ([("hase_step_fam.cu", "hase_step_f%d.cu.o" % f, ["-DHASE_FAM=%d" % f]) for f in range(FAMILIES)]
+         + [(s, s + ".o", []) for s in ("hase_kernels.cu", "hase_api.cu", "hase_serve.cu")])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]
@@ -57,12 +60,12 @@ def build(force=False, verbose=False, ptxas_info=False):
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
     objs, procs = [], []
-    for src in SOURCES:
+    for src, obj, extra in UNITS:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
+        o = os.path.join(BUILD, obj)
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
+            cmd = [nvcc()] + ARCH + FLAGS + extra + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT,

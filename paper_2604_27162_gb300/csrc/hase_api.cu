@@ -13,6 +13,7 @@
 
 #include "../../include/hase.h"
 #include "hase_internal.cuh"
+#include "hase_stream_plan.h"
 
 namespace hase {
 cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_envs, uint32_t key0,
@@ -20,8 +21,8 @@ cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_en
                             cudaStream_t st);
 cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* pos,
                            const uint64_t* rows, uint64_t* obs, uint8_t* unp, cudaStream_t st);
-cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
-                        cudaStream_t st);
+cudaError_t launch_step(int family, bool stream, const StepParams& p, uint32_t n_groups, uint32_t threads,
+                        uint32_t smem, cudaStream_t st);
 cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st);
 cudaError_t launch_central_init(const EnvRT* env, uint32_t n_envs, const uint16_t* pos, const uint64_t* rows,
                                 const uint32_t* coff, uint64_t* central, cudaStream_t st);
@@ -65,10 +66,12 @@ struct hase_handle {
     uint64_t agents = 0, obs_words = 0, unp_bytes = 0, rows_words = 0;
     uint32_t smem = 0, threads = 0, kc = 16, emit_warps = 0, steps_per_launch = 0, n_dyn = 1;
     uint32_t smem_budget = kSmemBudget;
+    bool waves = false;  // more CTAs than SMs (the batch is grouped one dynamics warp a CTA)
     // launches of one step: the groups of each kernel family (contiguous)
     struct Family {
         int fam;
         uint32_t first, count, smem, n_dyn, emit_warps, threads;
+        bool stream;  // the streaming form (stream_kernel) runs this family
     };
     std::vector<Family> fams;
     std::vector<EnvState> est0;  // episode clocks at create / reset
@@ -178,6 +181,23 @@ static uint64_t shape_key(const EnvRT& E) {
            (uint64_t)E.n_seekers;
 }
 
+// The streaming form runs families 1-8 unless the handle exports the
+// centralized observation or the fog of war (or asks for the chunked form).
+static bool streams(const hase_handle* h, int fam) {
+    // the emission warps write the steps of up to kStreamRing + one block of
+    // items in any order: their output slots must all differ
+    const bool can = fam >= 1 && fam <= 8 && !(h->base_flags & (kFog | kCentral)) && h->ring >= kStreamMinOutRing;
+    if (!can || (h->flags & HASE_CHUNKED_STEP)) return false;
+    // measured: the streaming form wins when CTAs run in waves (65,536 uneven
+    // envs: +13 %) and loses with one CTA per SM (1024 envs x 10 agents: -4 %)
+    return (h->flags & HASE_STREAM_STEP) || h->waves;
+}
+
+static bool plan_for(const hase_handle* h, const EnvRT* envs, int n, uint16_t flags, GroupPlan& plan) {
+    if (n > 0 && streams(h, family_of(envs[0]))) return plan_stream(envs, n, flags, plan);
+    return plan_group(envs, n, (int)h->kc, flags, plan);
+}
+
 static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
     const uint32_t E = h->n_envs;
     h->env_list.resize(E);
@@ -195,6 +215,7 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
     else
         epc = kMaxGroupEnvs;  // bounded by one dynamics warp below
     const bool many = !max_envs_cfg && E > 16u * n_sm;
+    h->waves = many;
     h->groups.clear();
     h->fams.clear();
     uint32_t smem_max = 0, dyn_max = 1;
@@ -218,8 +239,7 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             if (many && g.n_slots + En.n_agents > 32u) break;
             genv.push_back(En);
             const uint16_t flags = h->base_flags;
-            if (!plan_group(genv.data(), (int)genv.size(), (int)h->kc, flags, plan) ||
-                plan.total > h->smem_budget) {
+            if (!plan_for(h, genv.data(), (int)genv.size(), flags, plan) || plan.total > h->smem_budget) {
                 genv.pop_back();
                 break;
             }
@@ -229,7 +249,7 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
         }
         if (g.n_envs == 0) return false;  // one env alone exceeds the budget
         uint16_t flags = h->base_flags;
-        plan_group(genv.data(), g.n_envs, (int)h->kc, flags | kUseTable, plan);
+        plan_for(h, genv.data(), g.n_envs, flags | kUseTable, plan);
         const int fam0 = family_of(genv[0]);
         if (plan.total <= h->smem_budget) {
             flags |= kUseTable;
@@ -237,14 +257,14 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             plan_group(genv.data(), g.n_envs, (int)h->kc, flags | kUseTable | kSharedTable, plan);
             if (plan.total <= h->smem_budget) flags |= kUseTable | kSharedTable;
         }
-        plan_group(genv.data(), g.n_envs, (int)h->kc, flags, plan);
+        plan_for(h, genv.data(), g.n_envs, flags, plan);
         g.flags = flags;
         g.n_dyn = (uint8_t)plan.n_dyn;
         smem_max = std::max(smem_max, plan.total);
         dyn_max = std::max(dyn_max, plan.n_dyn);
         const int fam = family_of(genv[0]);
         if (h->fams.empty() || h->fams.back().fam != fam)
-            h->fams.push_back({fam, (uint32_t)h->groups.size(), 0u, 0u, 1u, 0u, 0u});
+            h->fams.push_back({fam, (uint32_t)h->groups.size(), 0u, 0u, 1u, 0u, 0u, streams(h, fam)});
         auto& F = h->fams.back();
         F.count += 1;
         F.smem = std::max(F.smem, plan.total);
@@ -273,10 +293,12 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         return fail(nullptr, HASE_EINVAL, "env ids exceed 32 bits");
     if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED | HASE_ASYNC_CREATE | HASE_POOL_ALLOC |
                        HASE_DESYNC_START | HASE_EXPORT_CENTRAL | HASE_EXPORT_STATE | HASE_SKIP_OBS |
-                       HASE_EXPORT_FOG | HASE_FOG_PER_AGENT))
+                       HASE_EXPORT_FOG | HASE_FOG_PER_AGENT | HASE_CHUNKED_STEP | HASE_STREAM_STEP))
         return fail(nullptr, HASE_EINVAL, "unknown flags 0x%x", cfg->flags);
     if ((cfg->flags & HASE_SKIP_OBS) && (cfg->flags & HASE_EXPORT_UNPACKED))
         return fail(nullptr, HASE_EINVAL, "HASE_EXPORT_UNPACKED needs the decentralized observation");
+    if ((cfg->flags & HASE_CHUNKED_STEP) && (cfg->flags & HASE_STREAM_STEP))
+        return fail(nullptr, HASE_EINVAL, "HASE_CHUNKED_STEP and HASE_STREAM_STEP exclude each other");
     if ((cfg->flags & HASE_FOG_PER_AGENT) && !(cfg->flags & HASE_EXPORT_FOG))
         return fail(nullptr, HASE_EINVAL, "HASE_FOG_PER_AGENT needs HASE_EXPORT_FOG");
     if (cfg->chunk_steps != 0 && (cfg->chunk_steps < 1 || cfg->chunk_steps > (uint32_t)kMaxChunk))
@@ -386,8 +408,9 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     for (auto& F : h->fams) {
         uint32_t M = cfg->emit_warps ? cfg->emit_warps : (!persistent ? 6u : (F.fam ? 9u : 12u));
         if (F.fam) M = std::min(M, 12u - F.n_dyn);
+        if (F.stream) M = std::max(1u, std::min(M, 11u - F.n_dyn));  // one more warp draws the actions
         F.emit_warps = M;
-        F.threads = 32 * (F.n_dyn + M);
+        F.threads = 32 * (F.n_dyn + M + (F.stream ? 1u : 0u));
         h->threads = std::max(h->threads, F.threads);
     }
     if (!h->emit_warps && !h->fams.empty()) h->emit_warps = h->fams[0].emit_warps;
@@ -617,11 +640,13 @@ static hase_status enqueue_steps(hase_handle* h, uint32_t n_steps, cudaStream_t 
         p.kc = h->kc;
         p.key0 = (uint32_t)(h->seed & 0xffffffffu);
         p.key1 = (uint32_t)(h->seed >> 32);
+        p.err = h->d_err;
         for (const auto& F : h->fams) {
             p.groups = h->d_groups + F.first;
             p.emit_warps = F.emit_warps;
             p.n_dyn = F.n_dyn;
-            HASE_CUDA(h, launch_step(F.fam, p, F.count, F.threads, F.smem, st));
+            p.dyn_ids = stream_dyn_ids((int)F.n_dyn, (int)(F.threads / 32), 0);
+            HASE_CUDA(h, launch_step(F.fam, F.stream, p, F.count, F.threads, F.smem, st));
         }
         done += n;
     }
@@ -841,11 +866,11 @@ hase_status hase_get_world(hase_handle* h, uint32_t e, uint8_t* grid, int32_t* s
 hase_status hase_sync(hase_handle* h) {
     if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
     HASE_CUDA(h, cudaDeviceSynchronize());
-    if (h->flags & HASE_ASYNC_CREATE) {
-        uint32_t herr = 0;
-        HASE_CUDA(h, cudaMemcpy(&herr, h->d_err, 4, cudaMemcpyDeviceToHost));
-        if (herr) return fail(h, HASE_EINVAL, "start-cell draw did not terminate");
-    }
+    uint32_t herr = 0;
+    HASE_CUDA(h, cudaMemcpy(&herr, h->d_err, 4, cudaMemcpyDeviceToHost));
+    if (herr & kErrWaitTimeout)
+        return fail(h, HASE_ETIMEOUT, "a bounded wait of the step kernel ran out; the outputs are incomplete");
+    if (herr) return fail(h, HASE_EINVAL, "start-cell draw did not terminate");
     return HASE_OK;
 }
 

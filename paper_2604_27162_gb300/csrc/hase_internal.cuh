@@ -113,6 +113,9 @@ struct GroupPlan {
     uint32_t max_side;                   // largest grid side of the group (sides may differ)
     uint32_t act_words;                  // uint32 words per action buffer
     uint32_t act, traj, rows, claim, tbl, state, fog, cen, total;  // byte offsets
+    uint32_t prist;                      // streaming form: pristine records (byte offset)
+    uint32_t rec_words;                  // streaming form: uint32 words of one (step, env) record
+    uint32_t ring;                       // streaming form: trajectory steps held on chip
     uint16_t flags;
 };
 
@@ -204,6 +207,82 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
     G.cen = align_up(G.fog + fo * 8, 16);                // uint64 [emit warps][2][4][side]
     const uint32_t cen_words = (flags & kCentral) ? kMaxEmitWarps * 8u * max_side : 0u;
     G.total = align_up(G.cen + cen_words * 8, 16);
+    G.prist = 0;
+    G.rec_words = 0;
+    G.ring = 0;
+    G.flags = flags;
+    return true;
+}
+
+// The streaming form of the step (stream_kernel): the dynamics warps write
+// one record per (step, env) into an on-chip trajectory ring -- the cell
+// x | y << sh of every agent as uint16, bit 15 of agent 0's entry set on the
+// step that ends the episode -- and the emission warps consume them behind
+// progress counters, with no block-wide barrier.  Record size by agent count.
+__host__ __device__ constexpr uint32_t stream_rec_words(uint32_t A) {
+    return A <= 2u ? 1u : (A <= 4u ? 2u : (A <= 8u ? 4u : 8u));
+}
+constexpr uint32_t kStreamRing = 64;   // trajectory steps on chip (power of two)
+constexpr uint32_t kActRing = 16;      // Philox blocks (quads of steps) per agent slot on chip (power of two)
+constexpr uint32_t kStreamGroup = 16;  // steps between the dynamics' progress updates
+constexpr uint32_t kStreamMinOutRing = 2 * kStreamRing + 32;  // output ring steps the streaming form needs
+constexpr uint32_t kErrWaitTimeout = 2u;  // error-word bit: a bounded wait of the step ran out
+
+// Shared-memory plan of one CTA of the streaming form (the dynamics state
+// bytes, obstacle rows and window tables as in plan_group; no claim words,
+// action buffers or chunk trajectories).
+__host__ __device__ inline bool plan_stream(const EnvRT* envs, int n, uint16_t flags, GroupPlan& G) {
+    uint32_t ro = 0, co = 0, to = 0, slot = 0, max_side = 0;
+    int dyn = 0;
+    uint32_t dyn_slots = 0;
+    G.dyn_first[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const EnvRT& E = envs[i];
+        if (dyn_slots + E.n_agents > 32u) {
+            if (dyn + 1 >= kMaxDyn) return false;
+            ++dyn;
+            G.dyn_first[dyn] = (uint8_t)slot;
+            dyn_slots = 0;
+        }
+        dyn_slots += E.n_agents;
+        G.first_slot[i] = (uint8_t)slot;
+        slot += E.n_agents;
+        max_side = E.side > max_side ? E.side : max_side;
+        G.rows_off[i] = ro;
+        ro += (uint32_t)(E.side + 2 * kPad) * E.rw;
+        G.cell_off[i] = co;
+        co += (1u << cell_shift(E)) * E.side;
+        G.fog_off[i] = 0;
+        for (int t = 0; t < 2; ++t) {
+            G.tbl_off[i][t] = ~0u;
+            if (!(flags & kUseTable) || !team_emits(E, t)) continue;
+            if (t == 1 && team_emits(E, 0) && E.r_hide == E.r_seek) {
+                G.tbl_off[i][1] = G.tbl_off[i][0];
+                continue;
+            }
+            G.tbl_off[i][t] = to;
+            to += (uint32_t)E.side * E.side * words_of_radius(team_radius(E, t));
+        }
+    }
+    G.fog_off[n] = 0;
+    G.n_dyn = (uint32_t)dyn + 1;
+    G.n_envs = (uint32_t)n;
+    G.max_side = max_side;
+    G.n_slots = slot;
+    G.dyn_first[dyn + 1] = (uint8_t)slot;
+    G.act_words = 0;
+    G.rec_words = n ? stream_rec_words(envs[0].n_agents) : 1u;
+    G.ring = kStreamRing;
+    G.traj = 0;                                                   // uint32 [ring][n][rec_words]
+    G.prist = align_up(G.traj + G.ring * (uint32_t)n * G.rec_words * 4u, 16);  // uint32 [n][rec_words]
+    G.rows = align_up(G.prist + (uint32_t)n * G.rec_words * 4u, 16);
+    G.tbl = align_up(G.rows + ro * 8, 16);
+    G.state = G.tbl + to * 8;                                     // uint8 per cell
+    G.claim = align_up(G.state + co, 16);                         // uint32 per cell
+    G.act_words = slot;                                           // uint32 action words of one quad
+    G.act = align_up(G.claim + co * 4, 16);                       // uint32 [kActRing][slots]
+    G.fog = G.cen = 0;
+    G.total = align_up(G.act + kActRing * slot * 4, 16);
     G.flags = flags;
     return true;
 }
@@ -268,6 +347,9 @@ struct StepParams {
     uint32_t n_dyn;      // dynamics warps per CTA (the largest group's)
     uint32_t emit_warps;
     uint32_t key0, key1;
+    uint32_t dyn_ids;           // streaming form: warp id of dynamics warp d in bits [4d, 4d + 4),
+                                // of the action warp in bits [16, 20)
+    uint32_t* err;              // error word (kErrWaitTimeout)
 };
 
 }  // namespace hase

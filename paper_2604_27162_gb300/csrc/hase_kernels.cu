@@ -365,10 +365,12 @@ cudaError_t launch_advance(uint64_t* clock, uint32_t n, cudaStream_t st) {
 }
 
 // The step kernel families live in their own translation units.
-#define HASE_FAMILY_DECL(f)                                                                            \
-    cudaError_t opt_in_f##f(int optin);                                                                \
-    cudaError_t launch_f##f(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem, \
-                            cudaStream_t st);
+#define HASE_FAMILY_DECL(f)                                                                                   \
+    cudaError_t opt_in_f##f(int optin);                                                                       \
+    cudaError_t launch_f##f(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,        \
+                            cudaStream_t st);                                                                 \
+    cudaError_t launch_stream_f##f(const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem, \
+                                   cudaStream_t st);
 HASE_FAMILY_DECL(0)
 HASE_FAMILY_DECL(1)
 HASE_FAMILY_DECL(2)
@@ -410,10 +412,23 @@ cudaError_t prepare_step(uint32_t smem) {
     return cudaSuccess;
 }
 
-// One launch of the groups of one kernel family.
-cudaError_t launch_step(int family, const StepParams& p, uint32_t n_groups, uint32_t threads, uint32_t smem,
-                        cudaStream_t st) {
+// One launch of the groups of one kernel family (stream: its streaming form).
+cudaError_t launch_step(int family, bool stream, const StepParams& p, uint32_t n_groups, uint32_t threads,
+                        uint32_t smem, cudaStream_t st) {
     if (n_groups == 0 || p.n_steps == 0) return cudaSuccess;
+    if (stream) {
+        switch (family) {
+            case 1: return launch_stream_f1(p, n_groups, threads, smem, st);
+            case 2: return launch_stream_f2(p, n_groups, threads, smem, st);
+            case 3: return launch_stream_f3(p, n_groups, threads, smem, st);
+            case 4: return launch_stream_f4(p, n_groups, threads, smem, st);
+            case 5: return launch_stream_f5(p, n_groups, threads, smem, st);
+            case 6: return launch_stream_f6(p, n_groups, threads, smem, st);
+            case 7: return launch_stream_f7(p, n_groups, threads, smem, st);
+            case 8: return launch_stream_f8(p, n_groups, threads, smem, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (family) {
         case 0: return launch_f0(p, n_groups, threads, smem, st);
         case 1: return launch_f1(p, n_groups, threads, smem, st);

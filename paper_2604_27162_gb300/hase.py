@@ -30,6 +30,9 @@ HASE_EXPORT_STATE = 64
 HASE_SKIP_OBS = 128
 HASE_EXPORT_FOG = 256
 HASE_FOG_PER_AGENT = 512
+HASE_CHUNKED_STEP = 1024
+HASE_STREAM_STEP = 2048
+STEP_FORMS = {"auto": 0, "chunked": HASE_CHUNKED_STEP, "stream": HASE_STREAM_STEP}
 HASE_OBS_LOS = 4
 HASE_OBS_SEEKERS = 1
 HASE_OBS_HIDERS = 2
@@ -420,7 +423,8 @@ class Engine:
     """One handle: create, step, and zero-copy torch views of the rings."""
 
     def __init__(self, n_envs, seed, descs, ring_steps, flags=0, env_id_base=0, stream=None,
-                 **tuning):
+                 step_form="auto", **tuning):
+        flags |= STEP_FORMS[step_form]  # auto: the engine's choice of step kernel form
         self.cfg = make_config(n_envs, seed, descs, ring_steps, flags, env_id_base, **tuning)
         self.stream = stream
         self.h = hase_create(self.cfg, stream)

@@ -29,25 +29,35 @@ def _cuda():
     hase.load()
 
 
-def test_plain16_full_run():
+# The two forms of the step kernel (identical outputs): the streaming one
+# (one-thread families without line of sight, centralized observation or fog
+# of war) and the chunked one.
+FORMS = {"stream": hase.HASE_STREAM_STEP, "chunked": hase.HASE_CHUNKED_STEP}
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_plain16_full_run(form):
     c = W.plain16()
-    compare_run(c["n_envs"], c["seed"], c["descs"], c["steps"])
+    compare_run(c["n_envs"], c["seed"], c["descs"], c["steps"], flags=hase.HASE_EXPORT_ACTIONS | FORMS[form])
 
 
-def test_ten_agents_1024_envs_600_steps():
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_ten_agents_1024_envs_600_steps(form):
     c = W.ten1k()
-    compare_run(1024, c["seed"], c["descs"], 600)
+    compare_run(1024, c["seed"], c["descs"], 600, flags=hase.HASE_EXPORT_ACTIONS | FORMS[form])
 
 
-def test_single_agent_packed_and_unpacked():
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_single_agent_packed_and_unpacked(form):
     c = W.single1k()
     compare_run(1024, c["seed"], c["descs"], 300,
-                flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED)
+                flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED | FORMS[form])
 
 
-def test_uneven_batch():
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_uneven_batch(form):
     descs = W.uneven_descs(1500, 3)
-    compare_run(1500, 3, descs, 300)
+    compare_run(1500, 3, descs, 300, flags=hase.HASE_EXPORT_ACTIONS | FORMS[form])
 
 
 @pytest.mark.parametrize("tuning", [
@@ -57,11 +67,13 @@ def test_uneven_batch():
     dict(chunk_steps=13, emit_warps=12, steps_per_launch=1),
     dict(chunk_steps=4, emit_warps=4, max_group_envs=3),
 ])
-def test_launch_configurations_agree(tuning):
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_launch_configurations_agree(tuning, form):
     c = W.ten1k()
     descs = [dict(c["descs"][0], cap=37)]
-    compare_run(70, c["seed"], descs, 90, **tuning)
-    compare_run(40, 11, W.uneven_descs(40, 5), 90, **tuning)
+    fl = hase.HASE_EXPORT_ACTIONS | FORMS[form]
+    compare_run(70, c["seed"], descs, 90, ring=200, flags=fl, **tuning)
+    compare_run(40, 11, W.uneven_descs(40, 5), 90, ring=170, flags=fl, **tuning)
 
 
 def test_graph_replays_match_oracle():
@@ -337,7 +349,9 @@ def test_invalid_configs_rejected():
         hase.Engine(4, 0, [good], 2, hase.HASE_SKIP_OBS | hase.HASE_EXPORT_UNPACKED)
     assert ei.value.status == hase.HASE_EINVAL
     with pytest.raises(hase.HaseError):
-        hase.Engine(4, 0, [good], 2, 1 << 10)  # unknown flag
+        hase.Engine(4, 0, [good], 2, 1 << 12)  # unknown flag
+    with pytest.raises(hase.HaseError):  # two step forms at once
+        hase.Engine(4, 0, [good], 2, hase.HASE_CHUNKED_STEP | hase.HASE_STREAM_STEP)
     with pytest.raises(hase.HaseError):  # per-agent maps without the fog export
         hase.Engine(4, 0, [good], 2, hase.HASE_FOG_PER_AGENT)
 
