@@ -63,6 +63,8 @@ constexpr uint16_t kFogAgent = 4;   // with kFog: one unit per observing agent
 constexpr uint16_t kSharedTable = 8;  // with kUseTable: one table of the larger emitting radius
                                       // serves both teams (line-of-sight families)
 constexpr uint16_t kCentral = 16;     // centralized observation: two row buffers per emission warp
+constexpr uint16_t kUnpStage = 32;    // streaming form: the unpacked export is staged in shared memory and
+                                      // written per step as one contiguous run (envs consecutive in the layout)
 
 // All envs of a group share the radii, the emitting teams, the row width and
 // the agent and seeker counts, so one code path serves the whole CTA.
@@ -116,6 +118,8 @@ struct GroupPlan {
     uint32_t prist;                      // streaming form: pristine records (byte offset)
     uint32_t rec_words;                  // streaming form: uint32 words of one (step, env) record
     uint32_t ring;                       // streaming form: trajectory steps held on chip
+    uint32_t stage, stage_bytes;         // streaming form: unpacked staging (byte offset, bytes per emission warp)
+    uint32_t unp_env;                    // streaming form: unpacked bytes of one env (uniform in the group)
     uint16_t flags;
 };
 
@@ -210,6 +214,7 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
     G.prist = 0;
     G.rec_words = 0;
     G.ring = 0;
+    G.stage = G.stage_bytes = G.unp_env = 0;
     G.flags = flags;
     return true;
 }
@@ -282,7 +287,19 @@ __host__ __device__ inline bool plan_stream(const EnvRT* envs, int n, uint16_t f
     G.act_words = slot;                                           // uint32 action words of one quad
     G.act = align_up(G.claim + co * 4, 16);                       // uint32 [kActRing][slots]
     G.fog = G.cen = 0;
-    G.total = align_up(G.act + kActRing * slot * 4, 16);
+    // unpacked bytes of one env: 3 (2r + 1)^2 per emitting agent
+    uint32_t unp = 0;
+    if (n > 0) {
+        const EnvRT& E = envs[0];
+        for (int a = 0; a < E.n_agents; ++a) {
+            const int t = a < E.n_seekers ? 0 : 1;
+            if (team_emits(E, t)) unp += 3u * (2u * team_radius(E, t) + 1u) * (2u * team_radius(E, t) + 1u);
+        }
+    }
+    G.unp_env = unp;
+    G.stage = align_up(G.act + kActRing * slot * 4, 16);          // uint8 [kMaxEmitWarps][stage_bytes]
+    G.stage_bytes = (flags & kUnpStage) ? align_up(32u * unp, 16) : 0u;
+    G.total = align_up(G.stage + kMaxEmitWarps * G.stage_bytes, 16);
     G.flags = flags;
     return true;
 }

@@ -27,10 +27,15 @@
 //     reuse ring slots.  One thread per item builds every observer's three
 //     planes with packed-byte window tests, the rewards and the done byte.
 //
+// With the unpacked export and envs consecutive in its layout, each emission
+// warp stages its block's unpacked bytes in shared memory and writes them per
+// step as one contiguous run (one 32-byte sector per warp store instead of a
+// sector per 4-byte store).
+//
 // Measured on a GB300 against the chunked form (step_kernel): +13 % on
-// 65,536 uneven envs (CTAs in waves), -4 % on 1024 envs x 10 agents (one CTA
-// per SM, where the dynamics chain of ~300 cycles a step under load bounds
-// both).  A warp-wide __match_any_sync over the targets was tried for the
+// 65,536 uneven envs (CTAs in waves), +38 % on 1024 envs x 2 agents with the
+// unpacked export, -4 % on 1024 envs x 10 agents (one CTA per SM, where the
+// dynamics chain of ~300 cycles a step under load bounds both).  A warp-wide __match_any_sync over the targets was tried for the
 // collision round and measured at ~800 cycles with ~30 distinct keys (~45
 // with a handful): its cost grows with the number of distinct keys.
 //
@@ -402,7 +407,7 @@ struct EmitPlan {
 // optional unpacked observation and true state).  sl: its ring slot.
 template <int A, bool W2>
 __device__ __forceinline__ void stream_item(const StepParams& P, const StreamShared& H, const EmitPlan& U,
-                                            uint32_t k, uint32_t e, uint32_t sl) {
+                                            uint32_t k, uint32_t e, uint32_t sl, uint8_t* stage_item) {
     constexpr int NS = (A + 1) / 2, NW = (A + 3) / 4;
     constexpr uint32_t RW = stream_rec_words(A);
     const EnvRT E = H.env[e];      // register copies: no later store can alias them
@@ -428,7 +433,9 @@ __device__ __forceinline__ void stream_item(const StepParams& P, const StreamSha
         TeamIn T;
         T.rows = U.base + ee.z;
         T.ob = P.obs + (uint64_t)sl * P.obs_words + E.obs_off;
-        T.unp = P.unp ? P.unp + (uint64_t)sl * P.unp_bytes : nullptr;
+        // the unpacked planes of agent a go to unp + unp_rel(a): the slot in
+        // global memory, or this item's place in the warp's staging area
+        T.unp = !P.unp ? nullptr : (stage_item ? stage_item - E.unp_off : P.unp + (uint64_t)sl * P.unp_bytes);
         T.slot = T.unp ? H.slot + H.plan.first_slot[e] : nullptr;
         T.side = E.side;
         T.rw = E.rw;
@@ -503,6 +510,8 @@ __device__ __forceinline__ void stream_emit(const StepParams& P, StreamShared& H
     U.ring_mask = L.ring - 1u;
     U.n_envs = ne;
     const uint32_t n_dyn_g = L.n_dyn;
+    uint8_t* const stage =
+        (L.flags & kUnpStage) && P.unp ? const_cast<uint8_t*>(sm) + L.stage + (uint32_t)ei * L.stage_bytes : nullptr;
     const uint32_t stride = 32u * (uint32_t)M;
     const uint32_t dk = stride / ne, de = stride % ne;
     uint32_t i = 32u * (uint32_t)ei + (uint32_t)lane;
@@ -515,8 +524,25 @@ __device__ __forceinline__ void stream_emit(const StepParams& P, StreamShared& H
             if (lane == 0) atomicOr(P.err, kErrWaitTimeout);
             return;
         }
-        if (i < n_items) stream_item<A, W2>(P, H, U, k, e, sl);
+        if (i < n_items) stream_item<A, W2>(P, H, U, k, e, sl, stage ? stage + lane * L.unp_env : nullptr);
         __syncwarp();  // every lane has read its record before the slots are handed back
+        if (stage) {
+            // the block's unpacked bytes, one contiguous run per step: envs
+            // e_a..e_b of step kk sit at unp_off[e_a] of its slot, and at
+            // (item - first item) * unp_env in the staging area
+            const uint32_t i0 = 32u * m, last = min(i0 + 31u, n_items - 1u);
+            const uint32_t k_a = i0 / ne, k_b = last / ne;
+            for (uint32_t kk = k_a; kk <= k_b; ++kk) {
+                const uint32_t first = max(i0, kk * ne), end = min(last + 1u, (kk + 1u) * ne);
+                const uint32_t e_a = first - kk * ne;
+                const uint32_t sl_k = __shfl_sync(0xffffffffu, sl, (int)(first - i0));
+                uint8_t* g = P.unp + (uint64_t)sl_k * P.unp_bytes + H.env[e_a].unp_off;
+                const uint8_t* src = stage + (first - i0) * L.unp_env;
+                const uint32_t len = (end - first) * L.unp_env;
+                for (uint32_t b = (uint32_t)lane; b < len; b += 32u) gst_u8(g + b, src[b]);
+            }
+            __syncwarp();  // the staging area is read before the next block writes it
+        }
         if (lane == 0) store_release(H.emit_prog + ei, min(n, (32u * (m + (uint32_t)M)) / ne));
         i += stride;
         e += de;
