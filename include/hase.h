@@ -73,14 +73,15 @@ typedef enum hase_status {
     HASE_EINVAL = 1,   /* invalid argument or configuration             */
     HASE_ENOMEM = 2,   /* device or host allocation failed              */
     HASE_ECUDA = 3,    /* a CUDA runtime call failed                    */
-    HASE_ETIMEOUT = 4, /* a bounded wait ran out                        */
-    HASE_EBUSY = 5,    /* resource temporarily unavailable (admission)  */
-    HASE_ESTATE = 6    /* call not valid in the handle's current state  */
+    HASE_ETIMEOUT = 4, /* a bounded wait ran out (hase_sync after the   */
+                       /* streaming step kernel; hase_server_poll)      */
+    HASE_EBUSY = 5,    /* hase_server_submit: the queue is full         */
+    HASE_ESTATE = 6    /* the server was shut down (hase_server_*)      */
 } hase_status;
 
 /* Limits of this implementation (checked at create). */
 #define HASE_MAX_SIDE 64
-#define HASE_MAX_AGENTS 16
+#define HASE_MAX_AGENTS 32
 #define HASE_MAX_RADIUS 4
 
 /* Configuration flags. */
@@ -220,28 +221,52 @@ typedef struct hase_digest_out {
 /* Create a batch on the current CUDA device: validates the configuration,
  * allocates every buffer, generates the worlds (a0) and writes the step -1
  * observation, all on `stream` (a cudaStream_t, NULL = legacy default).
+ * [Sec. 3.2: a grid world with blocking tiles, here seeded Bernoulli maps;
+ * Sec. 4.2: the generated world is kept as the pristine template; Sec. 3.3:
+ * a vectorized batch of independent environments.]
  * Returns HASE_EINVAL for a bad configuration, HASE_ENOMEM when device
  * memory runs out, HASE_ECUDA for other CUDA errors; *out is NULL then. */
 hase_status hase_create(const hase_config *cfg, void *stream, hase_handle **out);
 
-/* Back to t = 0: start cells, episode counters 0, step -1 observation. */
+/* Back to t = 0: start cells, episode counters 0 (or the desynchronised
+ * offsets), step -1 observation.  [Sec. 4.2: a reset restores the pristine
+ * initial state.] */
 hase_status hase_reset(hase_handle *h, void *stream);
 
 /* Enqueue n_steps steps (a1-a9) of every environment on `stream`.
- * Asynchronous; n_steps = 0 is a no-op. */
+ * Asynchronous; n_steps = 0 is a no-op; HASE_EINVAL when the step counter
+ * would pass 2^34.  A bounded wait of the streaming step kernel that ran out
+ * is reported later by hase_sync as HASE_ETIMEOUT.  [Sec. 3.1: one
+ * transition of the Dec-POMDP -- joint action, next state, per-agent
+ * observation and reward; Sec. 3.3: every environment of the batch.] */
 hase_status hase_step(hase_handle *h, uint32_t n_steps, void *stream);
 
-/* Device pointers of the output rings (NULL when the output is not kept). */
+/* Device pointers of the output rings (NULL when the output is not kept),
+ * owned by the handle, valid until hase_destroy.  [Sec. 4.3: the outputs are
+ * exposed in place, without a copy (the paper's zero-copy bridge, here in
+ * device memory).]
+ *   obs:     packed planes, and the uint8 unpacked ones  [Sec. 3.3, mode 1]
+ *   reward:  int32 per agent                             [Sec. 3.1, R]
+ *   done:    uint8 per env, 3 on the truncating step     [Sec. 4.2]
+ *   actions: uint8 per agent (HASE_EXPORT_ACTIONS)       [Sec. 4.1: random
+ *            actions are drawn inside the step] */
 hase_status hase_obs_ptr(hase_handle *h, uint64_t **packed, uint8_t **unpacked);
 hase_status hase_reward_ptr(hase_handle *h, int32_t **reward);
 hase_status hase_done_ptr(hase_handle *h, uint8_t **done);
 hase_status hase_actions_ptr(hase_handle *h, uint8_t **actions);
+/* The centralized-observation ring (HASE_EXPORT_CENTRAL; NULL without it).
+ * [Sec. 3.3, mode 3.] */
 hase_status hase_central_ptr(hase_handle *h, uint64_t **central);
 /* The true-state rings (HASE_EXPORT_STATE; NULL without it): cells
- * [ring_steps][agents] and ep_t [ring_steps][n_envs]. */
+ * [ring_steps][agents] and ep_t [ring_steps][n_envs].  [Sec. 3.3, modes 2,
+ * 4, 5.] */
 hase_status hase_state_ptr(hase_handle *h, uint16_t **cells, uint32_t **ep_t);
-/* The fog-of-war ring (HASE_EXPORT_FOG; NULL without it). */
+/* The fog-of-war ring (HASE_EXPORT_FOG; NULL without it).  [Sec. 3.3 and
+ * the discovery-map layer of Sec. 4; the newly discovered plane is the diff
+ * sweep of Sec. 5.] */
 hase_status hase_fog_ptr(hase_handle *h, uint64_t **fog);
+/* Sizes and per-env offsets of a ring slot.  [Sec. 4.1: the arena's per-env
+ * strides, here per-env offsets into each output.] */
 hase_status hase_layout_get(hase_handle *h, hase_layout *out);
 
 /* The same n_steps as one CUDA graph: the first call for a given n_steps
@@ -265,40 +290,50 @@ hase_status hase_digest(hase_handle *h, uint32_t n_steps, hase_digest_out *out, 
 
 /* hase_digest without any allocation: the same reduction and results, with
  * the partial sums of its first pass in a fixed device array of the library
- * (at most 256 partial sums of 3 words, 6 KiB) instead of the handle's
- * scratch.  Nothing in that array needs to start at zero (every slot read is
- * written first in the same call).  The first call on a device looks up the
- * array's address (cudaGetSymbolAddress, with the handle's device current);
- * make it before any stream capture.  Calls that overlap in time -- on any
- * handle or stream of the device -- race on the one array; serialise them.
- * A digest that needs more partial sums than the array holds is rejected
- * with HASE_EINVAL.  The paper has no counterpart: a scratch-free form of the
- * run summary for callers that may not allocate. */
+ * (256 partial sums of 3 words, 6 KiB) instead of the handle's scratch.  The
+ * first pass runs at most 256 blocks that stride over the outputs, so a
+ * digest of any length fits the array.  Nothing in that array needs to start
+ * at zero (every slot read is written first in the same call).  The first
+ * call on a device looks up the array's address (cudaGetSymbolAddress, with
+ * the handle's device current) and keeps it for the process: make that call
+ * before any stream capture, and not across a cudaDeviceReset of the device
+ * (the kept address would then be stale).  Calls that overlap in time -- on
+ * any handle or stream of the device -- race on the one array; serialise
+ * them.  The paper has no counterpart: a scratch-free form of the run
+ * summary for callers that may not allocate. */
 hase_status hase_digest_noalloc(hase_handle *h, uint32_t n_steps, hase_digest_out *out, int64_t *agent_rew,
                                 void *stream);
 
-/* Steps taken since create / reset. */
+/* Steps taken since create / reset (the t of the action counters).
+ * [Sec. 3.1: the time index of the transition.] */
 hase_status hase_step_count(hase_handle *h, uint64_t *t);
 
-/* Checkpoint: the dynamic state (positions, episode counters, step count)
- * as an opaque host blob.  hase_get_state with buf = NULL stores the size
- * in *size.  Both synchronize `stream`. */
+/* Checkpoint: the dynamic state (positions, episode counters, step count,
+ * fog-of-war maps) as an opaque host blob.  hase_get_state with buf = NULL
+ * stores the size in *size.  Both synchronize `stream`.  Not in the paper
+ * (its closest relative is the pristine template of Sec. 4.2). */
 hase_status hase_get_state(hase_handle *h, void *buf, size_t *size, void *stream);
 hase_status hase_set_state(hase_handle *h, const void *buf, size_t size, void *stream);
 
 /* Read back the pristine obstacle grid of env e (side*side bytes, row
- * major, 1 = obstacle) and the start cells (x, y per agent).  Synchronous. */
+ * major, 1 = obstacle) and the start cells (x, y per agent).  Synchronous.
+ * [Sec. 3.2: the generated world.] */
 hase_status hase_get_world(hase_handle *h, uint32_t e, uint8_t *grid, int32_t *start_xy);
 
-/* Wait for all work the handle enqueued. */
+/* Wait for all work the handle enqueued; HASE_ETIMEOUT when a bounded wait
+ * of the streaming step kernel ran out (its outputs are then incomplete),
+ * HASE_EINVAL when the world generation failed.  Not in the paper. */
 hase_status hase_sync(hase_handle *h);
 
 /* Number of CTAs and dynamic shared memory of one step launch, and the
- * fused steps per launch (for reports and the autotuner). */
+ * fused steps per launch (for reports and the autotuner).  Not in the paper. */
 hase_status hase_launch_info(hase_handle *h, uint32_t *ctas, uint32_t *threads,
                              uint32_t *smem_bytes, uint32_t *steps_per_launch);
 
+/* Free every buffer of the handle (NULL: no-op).  Not in the paper. */
 void hase_destroy(hase_handle *h);
+/* The message of the handle's last failure (NULL: of the last failed
+ * hase_create), owned by the library.  Not in the paper. */
 const char *hase_last_error(const hase_handle *h);
 
 #ifdef __cplusplus

@@ -427,15 +427,18 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
 
     h->last_stream = st;
     if (h->flags & HASE_POOL_ALLOC) {
-        // keep freed pool memory cached for the next handles (once per device)
-        static int pool_ready[64] = {0};
+        // keep freed pool memory cached for the next handles (once per device;
+        // handles may be created from several threads)
+        static std::mutex pool_mu;
+        static bool pool_ready[64] = {false};
+        std::lock_guard<std::mutex> lock(pool_mu);
         if (h->device >= 0 && h->device < 64 && !pool_ready[h->device]) {
             cudaMemPool_t mp;
             if (cudaDeviceGetDefaultMemPool(&mp, h->device) == cudaSuccess) {
                 uint64_t thr = ~0ull;
                 cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
             }
-            pool_ready[h->device] = 1;
+            pool_ready[h->device] = true;
         }
     }
     auto alloc = [&](void** p, size_t bytes) -> cudaError_t {
@@ -908,9 +911,11 @@ hase_status hase_digest_noalloc(hase_handle* h, uint32_t n_steps, hase_digest_ou
         std::lock_guard<std::mutex> lock(mu);
         if (!addr[dev]) HASE_CUDA(h, digest_scratch_address(&addr[dev], &words[dev]));
     }
+    // digest_parts caps the first pass at kDigestBlocks blocks, which stride
+    // over the outputs: every digest fits the array (a consistency check)
     const uint32_t n_part = digest_parts(h, n_steps);
     if ((uint64_t)3 * n_part > words[dev])
-        return fail(h, HASE_EINVAL, "digest needs %u partial sums, the static scratch holds %zu", n_part,
+        return fail(h, HASE_ECUDA, "internal: %u partial sums exceed the static scratch (%zu)", n_part,
                     words[dev] / 3);
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;

@@ -21,7 +21,8 @@
 namespace hase {
 
 constexpr int kPad = 4;               // padding cells around the grid (max radius)
-constexpr int kMaxAgents = 16;        // agents per env
+constexpr int kMaxAgents = 32;        // agents per env (one dynamics lane each, whole envs per warp)
+constexpr int kFastAgents = 16;       // agents per env of the one-thread emission families 1-16
 constexpr int kMaxGroupEnvs = 64;     // envs per CTA
 constexpr int kMaxGroupSlots = 128;   // agents per CTA (four dynamics warps)
 constexpr int kMaxDyn = 4;            // dynamics warps per CTA
@@ -124,10 +125,10 @@ struct GroupPlan {
 };
 
 // One thread emits a whole (step, env) when the seekers are the first
-// ceil(A / 2) agents (windows of up to two words a plane); other shapes take
-// the lane-per-agent emission.
+// ceil(A / 2) of at most 16 agents (windows of up to two words a plane);
+// other shapes take the lane-per-agent emission.
 __host__ __device__ inline bool fast_emission(const EnvRT& E) {
-    return E.wpp <= 2 && E.n_seekers == (E.n_agents + 1u) / 2u;
+    return E.wpp <= 2 && E.n_agents <= (uint32_t)kFastAgents && E.n_seekers == (E.n_agents + 1u) / 2u;
 }
 
 // Kernel families: family 0 runs the general (lane per agent) emission;

@@ -9,6 +9,8 @@
 //   digest kernels  the run summary of hase_digest / hase_digest_noalloc
 //   advance_kernel  the device step counter
 // and the host launchers; the step kernel itself is in hase_step.cuh.
+#include <mutex>
+
 #include "hase_step.cuh"
 
 namespace hase {
@@ -398,7 +400,9 @@ cudaError_t prepare_step(uint32_t smem) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    static int done[64] = {0};
+    static std::mutex mu;  // handles may be created from several threads
+    static bool done[64] = {false};
+    std::lock_guard<std::mutex> lock(mu);
     if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
@@ -408,7 +412,7 @@ cudaError_t prepare_step(uint32_t smem) {
                                  opt_in_f13, opt_in_f14, opt_in_f15, opt_in_f16};
     for (auto f : opt)
         if ((e = f(optin)) != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) done[dev] = 1;
+    if (dev >= 0 && dev < 64) done[dev] = true;
     return cudaSuccess;
 }
 

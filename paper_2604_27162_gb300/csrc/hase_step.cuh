@@ -244,10 +244,11 @@ __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.
 // Centralized observation of one (step, env) by one half-warp (16 lanes;
 // the two halves of a warp build two blocks at once), in a buffer of 4 S
 // words of shared memory laid out as the output block ([4][S]: seen, seen
-// obstacles, seen seekers, seen hiders).  Lane a (< A <= 16) of the half ORs
-// its cell into the seeker or hider rows (words 2S.., 3S..) and, if its team
-// observes, its window rows (with line of sight: only the visible cells,
-// from one visibility mask) into the seen rows; then the half's lanes turn
+// obstacles, seen seekers, seen hiders).  Lane hl of the half takes agents
+// hl, hl + 16 (A <= 32): it ORs each one's cell into the seeker or hider rows
+// (words 2S.., 3S..) and, if its team observes, its window rows (with line of
+// sight: only the visible cells, from one visibility mask) into the seen
+// rows; then the half's lanes turn
 // rows into output values in place, 16 rows at a time, and its lane 0
 // copies the block to global memory with one bulk copy.  `live`: this half
 // has an item (the warp's barriers are taken by all 32 lanes either way).
@@ -259,10 +260,10 @@ __device__ inline void central_half(const EnvRT& E, const uint64_t* rows, const 
     if (live)
         for (int y = hl; y < 4 * S; y += 16) buf[y] = 0ull;
     __syncwarp();
-    if (live && hl < A) {
-        const uint32_t v = src[hl] & 0x0fffu;
+    for (int a = hl; live && a < A; a += 16) {
+        const uint32_t v = src[a] & 0x0fffu;
         const int xa = (int)(v & ((1u << sh) - 1u)), ya = (int)(v >> sh);
-        const int team = hl < ns ? 0 : 1;
+        const int team = a < ns ? 0 : 1;
         const bool wide = S > 32;
         or_row(buf + (team ? 3 * S : 2 * S) + ya, 1ull << xa, wide);
         if (team_sees(E, team)) {
@@ -497,7 +498,6 @@ __device__ __forceinline__ void emit_chunk(const StepParams& P, const CtaShared&
         const uint32_t sh = cell_shift(H.env[ee]), xmask = (1u << sh) - 1u;
         const uint16_t* Tk = C.T + kk * nsl + first;
         const bool done = (Tk[0] & kDoneBit) != 0u;
-        int x[AM], y[AM];
         uint32_t myseen = 0;  // seeker lanes: hiders b seen by this seeker
         if (done) {
             // the reward's "seen" test on the pre-reset positions
@@ -510,23 +510,10 @@ __device__ __forceinline__ void emit_chunk(const StepParams& P, const CtaShared&
                 const int dx = abs((int)(v & xmask) - xa), dy = abs((int)(v >> sh) - ya);
                 if (!ta && b >= ns) myseen |= (uint32_t)(max(dx, dy) <= rs) << b;
             }
-#pragma unroll
-            for (int b = 0; b < AM; ++b) {
-                if (b >= A) break;
-                const uint32_t p = H.slot[first + b].p0;
-                x[b] = (int)(p & xmask);
-                y[b] = (int)(p >> sh);
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b < AM; ++b) {
-                if (b >= A) break;
-                const uint32_t v = Tk[b];
-                x[b] = (int)(v & xmask);
-                y[b] = (int)((v & 0x0fffu) >> sh);
-            }
         }
-        const uint32_t po = done ? (uint32_t)H.slot[first + a].p0 : (Tk[a] & 0x0fffu);
+        // the observed positions: the pristine start cells after a reset
+        const uint16_t* src = done ? H.p0 + first : Tk;
+        const uint32_t po = src[a] & 0x0fffu;
         const int xo = (int)(po & xmask), yo = (int)(po >> sh);
         const int xra = xo - R, yra = yo - R;
         Plane<NW> ps, ph;  // bits of seekers / hiders in this agent's window
@@ -535,7 +522,8 @@ __device__ __forceinline__ void emit_chunk(const StepParams& P, const CtaShared&
 #pragma unroll
         for (int b = 0; b < AM; ++b) {
             if (b >= A) break;
-            const uint32_t dx = (uint32_t)(x[b] - xra), dy = (uint32_t)(y[b] - yra);
+            const uint32_t v = src[b] & 0x0fffu;
+            const uint32_t dx = (uint32_t)((int)(v & xmask) - xra), dy = (uint32_t)((int)(v >> sh) - yra);
             const bool in = (max(dx, dy) <= twoR) && b != a;
             const uint32_t bit = dy * (uint32_t)D + dx;
             if (b < ns) {

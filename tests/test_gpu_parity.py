@@ -335,7 +335,7 @@ def test_world_readback_matches_oracle():
 
 def test_invalid_configs_rejected():
     good = W.ten1k()["descs"][0]
-    for bad in (dict(good, side=65), dict(good, side=1), dict(good, n_agents=17),
+    for bad in (dict(good, side=65), dict(good, side=1), dict(good, n_agents=33),
                 dict(good, n_agents=0), dict(good, n_seekers=11), dict(good, r_seek=5),
                 dict(good, cap=0), dict(good, obs_teams=8)):
         with pytest.raises(hase.HaseError) as ei:
@@ -359,17 +359,27 @@ def test_invalid_configs_rejected():
 # ---------------------------------------------------------------------------
 # Full-size runs in the benchmark's launch configuration.
 # ---------------------------------------------------------------------------
-def _full_size_check(cfg, n_steps, sample_envs, flags=0):
+def _full_size_check(cfg, n_steps, sample_envs, flags=0, setting=None, graph=False):
+    """The workload at full size in the benchmark's launch configuration
+    (setting: an autotuned launch setting; graph: the steps replayed as one
+    CUDA graph), then: the done property over every env and step on the GPU,
+    and every output of every step of the sampled envs against a one-env
+    oracle (the unpacked export too when the flags ask for it)."""
     import torch
 
     n = cfg["n_envs"]
     descs = cfg["descs"]
-    eng = hase.Engine(n, cfg["seed"], descs, n_steps, flags)
-    eng.step(n_steps)
+    eng = hase.Engine(n, cfg["seed"], descs, n_steps, flags, **(setting or {}))
+    if graph:
+        eng.step_graph(n_steps)
+    else:
+        eng.step(n_steps)
     torch.cuda.synchronize()
     L = eng.layout
     aoff = L["agent_off"].astype(np.int64)
     ooff = L["obs_off"].astype(np.int64)
+    uoff = L["unp_off"].astype(np.int64)
+    unpacked = bool(flags & hase.HASE_EXPORT_UNPACKED)
     # properties over every env and step (on the GPU)
     done = eng.done
     caps = torch.tensor([descs[0 if len(descs) == 1 else e]["cap"] for e in range(n)],
@@ -382,13 +392,16 @@ def _full_size_check(cfg, n_steps, sample_envs, flags=0):
         d = descs[0 if len(descs) == 1 else e]
         rew = eng.reward[:, aoff[e]:aoff[e + 1]].cpu().numpy()
         obs = eng.obs[:, ooff[e]:ooff[e + 1]].cpu().numpy().view(np.uint64)
+        unp = eng.unpacked[:, uoff[e]:uoff[e + 1]].cpu().numpy() if unpacked else None
         dn = eng.done[:, e].cpu().numpy()
         w = oracle.World(1, cfg["seed"], [d], env_id_base=e)
         for t in range(n_steps):
-            o = w.step()
+            o = w.step(unpacked=unpacked)
             assert (rew[t] == o["reward"]).all(), (e, t)
             assert (obs[t] == o["obs"]).all(), (e, t)
             assert dn[t] == o["done"][0], (e, t)
+            if unpacked:
+                assert (unp[t] == o["unpacked"]).all(), (e, t)
     eng.close()
 
 
@@ -398,8 +411,9 @@ def test_full_size_ten_agents_sampled():
 
 
 def test_full_size_single_agent_sampled():
+    """The whole 10,000-step run of the benchmark, packed and unpacked."""
     cfg = W.single1k()
-    _full_size_check(cfg, 3000, [0, 5, 700, 1023], flags=hase.HASE_EXPORT_UNPACKED)
+    _full_size_check(cfg, cfg["steps"], [0, 5, 700, 1023], flags=hase.HASE_EXPORT_UNPACKED)
 
 
 def test_full_size_line_of_sight_sampled():
@@ -411,3 +425,61 @@ def test_full_size_line_of_sight_sampled():
 def test_full_size_uneven_sampled():
     cfg = W.uneven64k()
     _full_size_check(cfg, 200, [0, 1, 4097, 33333, 65535])
+
+
+def _uneven_samples(descs, per_key=1):
+    """Envs of the uneven table spread over sides, agent counts and radii."""
+    picks, seen = [], set()
+    for e, d in enumerate(descs):
+        for key in (("side", d["side"]), ("agents", d["n_agents"]), ("radius", d["r_seek"])):
+            if key not in seen:
+                seen.add(key)
+                picks.append(e)
+    return sorted(set(picks))
+
+
+def test_full_size_uneven_autotuned_graph():
+    """The benchmark's batched form of the uneven workload: the autotuned
+    setting, the 1,000-step rollout replayed as one CUDA graph."""
+    from paper_2604_27162_gb300 import autotune
+
+    cfg = W.uneven64k()
+    setting, _ = autotune.tune(cfg["n_envs"], cfg["seed"], cfg["descs"])
+    sample = _uneven_samples(cfg["descs"])
+    assert len(sample) >= 8
+    _full_size_check(cfg, cfg["steps"], sample, setting=setting, graph=True)
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+@pytest.mark.parametrize("rank", [1, 3])
+def test_rank_shards_match_oracle(rank, form):
+    """The env range of rank 1 or 3 of a multi-GPU run (env ids from
+    rank * 1024): its draws are keyed by the global env ids."""
+    c = W.ten1k()
+    compare_run(1024, c["seed"], c["descs"], 200, flags=hase.HASE_EXPORT_ACTIONS | FORMS[form],
+                env_id_base=rank * 1024)
+
+
+TWENTY_PLUS = [
+    W.env_desc(32, 20, 10, 3, 2, 37, "0.2"),    # the paper's 20 searchers (seekers = ceil(A / 2))
+    W.env_desc(24, 20, 12, 2, 3, 29, "0.15"),   # seekers != ceil(A / 2)
+    W.env_desc(16, 32, 5, 1, 2, 23, "0.1"),     # 32 agents, few seekers
+    W.env_desc(64, 32, 16, 4, 4, 41, "0.25"),   # 32 agents on the largest grid, radius 4
+]
+
+
+def test_twenty_and_thirty_two_agents():
+    """Up to 32 agents an env (one dynamics lane each): the lane-per-agent
+    emission, alone and mixed in one batch."""
+    for d in TWENTY_PLUS:
+        compare_run(12, 31, [d], 120)
+    descs = [TWENTY_PLUS[e % 4] for e in range(40)]
+    compare_run(40, 32, descs, 100, launches=[37, 63])
+
+
+def test_thirty_two_agents_optional_exports():
+    descs = [dict(TWENTY_PLUS[e % 4], obs_teams=3 | (4 if e % 2 else 0)) for e in range(16)]
+    flags = (hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_CENTRAL | hase.HASE_EXPORT_STATE
+             | hase.HASE_EXPORT_FOG | hase.HASE_EXPORT_UNPACKED)
+    compare_run(16, 33, descs, 90, flags=flags)
+    compare_run(16, 34, descs, 60, flags=flags | hase.HASE_FOG_PER_AGENT | hase.HASE_DESYNC_START)

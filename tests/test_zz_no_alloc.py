@@ -44,7 +44,25 @@ def test_noalloc_digest_equals_digest_twice(case):
     eng.step(33)
     a, b, ra, rb = _both(eng, eng.ring)  # after more steps, the whole ring
     assert np.array_equal(a, b) and np.array_equal(ra, rb)
-    with pytest.raises(hase.HaseError):
-        # longer than the ring: rejected by the argument checks, before any launch
-        hase.hase_digest_noalloc(eng.h, eng.ring + 1, 0)
+    eng.close()
+
+
+def test_noalloc_digest_rejects_bad_lengths():
+    """The argument checks run before any launch, with a valid output
+    pointer, so that each bound is the one that fires."""
+    import torch
+
+    c = W.ten1k()
+    eng = hase.Engine(64, c["seed"], c["descs"], ring_steps=40)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    eng.step(10)
+    for n, why in ((eng.ring + 1, "n_steps must be in"), (0, "n_steps must be in"), (11, "n_steps must be in")):
+        with pytest.raises(hase.HaseError) as ei:
+            hase.hase_digest_noalloc(eng.h, n, out.data_ptr(), None, eng.stream)
+        assert ei.value.status == hase.HASE_EINVAL and why in str(ei.value), (n, str(ei.value))
+    with pytest.raises(hase.HaseError) as ei:  # no output pointer
+        hase.hase_digest_noalloc(eng.h, 5, 0, None, eng.stream)
+    assert "out is NULL" in str(ei.value)
+    hase.hase_digest_noalloc(eng.h, 10, out.data_ptr(), None, eng.stream)  # the bounds themselves are accepted
+    torch.cuda.synchronize()
     eng.close()
