@@ -532,40 +532,56 @@ def request_bytes_algorithmic(r):
 
 def run_served(args):
     """Served rollouts: the Poisson request stream through the rollout server
-    (continuous batching under the HBM budget), and the same stream's first
-    seconds served one request at a time for comparison."""
+    (continuous batching into shared launches under the HBM budget); the
+    server's capacity (the same stream submitted at once) and p50/p99 latency
+    against the arrival rate; the stream served with every request in its own
+    handle (no shared launches) for comparison; the oracle on a sample of the
+    requests as the CPU baseline."""
     import torch
 
     from paper_2604_27162_gb300 import hase
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     hase.load()
-    reqs = W.served_requests(duration=args.duration)
     budget = int(args.budget_gb * (1 << 30))
 
-    def summarize(res, reqs_, makespan):
+    def summarize(res, reqs_):
         ok = [i for i, r in enumerate(res) if r["status"] == hase.HASE_OK]
-        lat = sorted(res[i]["finished"] - reqs_[i]["arrival"] for i in ok)
+        lat = sorted(res[i]["finished"] - res[i]["submitted"] for i in ok)
+        span = max((res[i]["finished"] for i in ok), default=0.0) - min((res[i]["submitted"] for i in ok), default=0.0)
         env_steps = sum(reqs_[i]["n_envs"] * reqs_[i]["steps"] for i in ok)
         agent_steps = sum(reqs_[i]["n_envs"] * reqs_[i]["steps"] * reqs_[i]["desc"]["n_agents"] for i in ok)
         q = lambda p: lat[min(len(lat) - 1, int(p * len(lat)))] if lat else None
         return {"requests": len(reqs_), "ok": len(ok), "env_steps": env_steps, "agent_steps": agent_steps,
-                "env_steps_per_s": env_steps / makespan, "agent_steps_per_s": agent_steps / makespan,
+                "env_steps_per_s": env_steps / span if span else None,
+                "agent_steps_per_s": agent_steps / span if span else None,
                 "p50_ms": q(0.50) * 1e3 if lat else None, "p99_ms": q(0.99) * 1e3 if lat else None,
-                "makespan_s": makespan}
+                "makespan_s": span,
+                "mean_batch": sum(res[i]["batch_size"] for i in ok) / max(1, len(ok))}
+
+    def serve(reqs_, time_scale, max_batch=0):
+        res, st = hase.hase_serve(reqs_, budget, n_streams=args.streams, max_inflight=4096, time_scale=time_scale,
+                                  max_batch=max_batch)
+        return summarize(res, reqs_), st, res
 
     hase.hase_serve(W.served_requests(duration=0.05), budget, n_streams=args.streams)  # warm-up
+    reqs = W.served_requests(duration=args.duration)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    res, stats = hase.hase_serve(reqs, budget, n_streams=args.streams, max_inflight=4096, time_scale=1.0)
+    s, stats, res = serve(reqs, 1.0)  # the stream at its own pace: 2,000 requests/s
     clk = clocks.stop()
-    s = summarize(res, reqs, stats["makespan"])
-    # the same stream's first seconds, one request at a time on one stream
-    head = [r for r in reqs if r["arrival"] < args.serial_seconds]
-    res1, st1 = hase.hase_serve(head, budget, n_streams=1, max_inflight=1, time_scale=1.0)
-    s1 = summarize(res1, head, st1["makespan"])
+    # capacity: a few seconds of the stream submitted at once; latency against rate
+    head = [r for r in reqs if r["arrival"] < args.sweep_seconds]
+    cap, _, _ = serve(head, 0.0)
+    sweep = []
+    for rate in args.rates:
+        sub = W.served_requests(rate=rate, duration=args.sweep_seconds)
+        r_, _, _ = serve(sub, 1.0)
+        sweep.append({"rate_per_s": rate, **{k: r_[k] for k in ("requests", "env_steps_per_s", "p50_ms", "p99_ms",
+                                                                  "mean_batch")}})
+    unshared, _, _ = serve(head, 0.0, max_batch=1)  # every request its own handle and launches
     alg = sum(request_bytes_algorithmic(reqs[i]) for i, r in enumerate(res) if r["status"] == hase.HASE_OK)
-    achieved = alg / stats["makespan"] / 1e9
+    achieved = alg / s["makespan_s"] / 1e9
     peak, peak_kind = peaks()
     out = {
         "metric": "env-steps/s",
@@ -576,7 +592,7 @@ def run_served(args):
         "n_gpus": 1,
         "steps": 1,
         "warmup": 1,
-        "ms_per_step": stats["makespan"] * 1e3,
+        "ms_per_step": s["makespan_s"] * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -587,21 +603,44 @@ def run_served(args):
             "rate_per_s": 2000.0, "duration_s": args.duration, "requests": s["requests"],
             "served_ok": s["ok"], "budget_gb": args.budget_gb, "streams": args.streams,
             "peak_bytes": stats["peak_bytes"], "peak_inflight": stats["peak_inflight"],
-            "rejected": stats["rejected"],
-            "one_at_a_time": {"seconds_of_stream": args.serial_seconds, **s1},
+            "rejected": stats["rejected"], "batches": stats["batches"], "mean_batch": s["mean_batch"],
+            "capacity": {"seconds_of_stream": args.sweep_seconds, "submitted_at_once": True, **cap},
+            "capacity_env_steps_per_s": cap["env_steps_per_s"],
+            "unshared": {"note": "the same requests, every one its own handle and launches", **unshared},
+            "rate_sweep": sweep,
             "l2": "outputs of every request resident until its digest (far above L2 in total)",
         },
         "roofline": {"bound": "hbm", "kernel": "step_kernel", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "note": "offered load, not capacity: the stream arrives at 2,000 requests/s"},
-        "gpu_launches": 4 * s["ok"],
+                     "note": "offered load of the 2,000 requests/s stream, not capacity (see config.capacity)"},
+        "gpu_launches": None,
         "clocks": clk,
         "e2e": {"value": s["env_steps_per_s"], "unit": "env-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 32,
                 "note": "the server is the public API: per request the 32-byte digest comes back"},
-        "cpu_baseline": None,
+        "cpu_baseline": None if args.no_cpu else served_cpu_baseline(reqs),
     }
     print(json.dumps(out))
+
+
+def served_cpu_baseline(reqs, target_s=10.0):
+    """The oracle on the host, one core: requests of the stream run back to
+    back (every step of every env, digest included) for about target_s."""
+    import oracle
+
+    t0 = time.perf_counter()
+    done_env = n = 0
+    for r in reqs:
+        w = oracle.World(r["n_envs"], r["seed"], [r["desc"]])
+        w.run_digest(r["steps"])
+        w.close()
+        n += 1
+        done_env += r["n_envs"] * r["steps"]
+        if time.perf_counter() - t0 > target_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done_env / dt, "unit": "env-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d requests of the stream, back to back (%.1f s)" % (n, dt)}
 
 
 def run_reference_served(args, world):
@@ -710,8 +749,10 @@ def main():
     ap.add_argument("--duration", type=float, default=60.0, help="served: seconds of the request stream")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="served: device memory budget")
     ap.add_argument("--streams", type=int, default=16, help="served: CUDA streams of the server")
-    ap.add_argument("--serial-seconds", type=float, default=5.0,
-                    help="served: seconds of the stream also served one request at a time")
+    ap.add_argument("--sweep-seconds", type=float, default=2.0,
+                    help="served: seconds of stream per capacity and rate-sweep point")
+    ap.add_argument("--rates", type=float, nargs="*", default=[1000.0, 2000.0, 4000.0, 8000.0, 16000.0],
+                    help="served: arrival rates of the latency sweep (requests/s)")
     ap.add_argument("--step-form", choices=sorted(H.STEP_FORMS), default="auto",
                     help="step kernel form: auto (the engine's choice; the batched form lets the autotuner "
                          "choose), chunked or stream")

@@ -186,6 +186,14 @@ typedef struct hase_config {
                                  /* (16384..221184), 0 = 221184: smaller caps  */
                                  /* pack fewer envs per CTA and drop window    */
                                  /* tables, so that more CTAs fit on an SM     */
+    const uint64_t *env_seeds;   /* NULL, or one Philox seed per env (host     */
+                                 /* array of n_envs): env e draws with its own */
+                                 /* key instead of `seed`                      */
+    const uint32_t *env_ids;     /* NULL, or the env id of every env in the    */
+                                 /* Philox counters (host array of n_envs)     */
+                                 /* instead of env_id_base + e.  With both, one */
+                                 /* handle holds envs of several independent  */
+                                 /* runs, each bit for bit as if run alone     */
 } hase_config;
 
 /* Sizes and per-env offsets of one ring slot.  The offset arrays are host
@@ -287,6 +295,17 @@ hase_status hase_step_graph(hase_handle *h, uint32_t n_steps, void *stream);
  * (OOPSLA 2014).  Not in the paper: a result summary for serving and tests. */
 hase_status hase_digest(hase_handle *h, uint32_t n_steps, hase_digest_out *out, int64_t *agent_rew,
                         void *stream);
+
+/* hase_digest over steps [first_step, first_step + n_steps) (all still in
+ * the ring) of envs [env_first, env_first + env_count): the digest index of
+ * an observation word is s * W + j, with W the range's words per slot and j
+ * the word's place inside the range, so that envs of several independent
+ * runs sharing a handle (hase_config.env_seeds, env_ids) each get the digest
+ * of their run alone.  agent_rew: per-agent sums of the range's agents.
+ * Same scratch rule as hase_digest.  Not in the paper: the result summary of
+ * one served request. */
+hase_status hase_digest_range(hase_handle *h, uint64_t first_step, uint32_t n_steps, uint32_t env_first,
+                              uint32_t env_count, hase_digest_out *out, int64_t *agent_rew, void *stream);
 
 /* hase_digest without any allocation: the same reduction and results, with
  * the partial sums of its first pass in a fixed device array of the library

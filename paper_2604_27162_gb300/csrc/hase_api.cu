@@ -16,9 +16,8 @@
 #include "hase_stream_plan.h"
 
 namespace hase {
-cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_envs, uint32_t key0,
-                            uint32_t key1, uint16_t* pos, uint16_t* start, uint64_t* rows, uint32_t* err,
-                            cudaStream_t st);
+cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_envs, const uint2* keys,
+                            uint16_t* pos, uint16_t* start, uint64_t* rows, uint32_t* err, cudaStream_t st);
 cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* pos,
                            const uint64_t* rows, uint64_t* obs, uint8_t* unp, cudaStream_t st);
 cudaError_t launch_step(int family, bool stream, const StepParams& p, uint32_t n_groups, uint32_t threads,
@@ -31,10 +30,9 @@ cudaError_t launch_state_init(const uint16_t* pos, const EnvState* est, uint32_t
 cudaError_t launch_fog_init(const EnvRT* env, uint32_t n_envs, const uint16_t* pos, const uint64_t* rows,
                             const uint32_t* foff, uint32_t per_agent, uint64_t* fog, uint64_t* state,
                             cudaStream_t st);
-cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
-                          uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
-                          uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
-                          int64_t* agent_rew, cudaStream_t st);
+cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, DigestSpan ow, DigestSpan ev,
+                          DigestSpan ag, uint32_t ring, uint64_t first, uint32_t n_steps, uint64_t* scratch,
+                          uint32_t n_part, const uint32_t* err, uint64_t* out, int64_t* agent_rew, cudaStream_t st);
 cudaError_t digest_scratch_address(uint64_t** p, size_t* words);
 cudaError_t prepare_step(uint32_t smem);
 }  // namespace hase
@@ -47,6 +45,8 @@ struct hase_handle {
     uint64_t seed = 0;
     std::vector<EnvRT> env;
     std::vector<uint32_t> thr;
+    std::vector<uint2> keys;  // per env: Philox key words
+    uint2* d_keys = nullptr;
     std::vector<Group> groups;
     std::vector<uint32_t> env_list;
     std::vector<uint64_t> agent_off, obs_off, unp_off, central_off;
@@ -129,7 +129,7 @@ static void free_all(hase_handle* h) {
     void* ptrs[] = {h->d_env, h->d_est,  h->d_pos, h->d_start, h->d_rows, h->d_groups,
                     h->d_obs, h->d_rew, h->d_done, h->d_act,  h->d_unp,  h->d_err, h->d_thr, h->d_env_list,
                     h->d_clock, h->d_scratch, h->d_central, h->d_coff, h->d_cells, h->d_ept,
-                    h->d_fog, h->d_fog_off, h->d_fog_state};
+                    h->d_fog, h->d_fog_off, h->d_fog_state, h->d_keys};
     const bool pool = h->flags & HASE_POOL_ALLOC;
     for (void* p : ptrs)
         if (p) {
@@ -167,6 +167,16 @@ static hase_status validate(const hase_env_desc& d, uint32_t i) {
     if (d.obs_teams > 7u) return fail(nullptr, HASE_EINVAL, "env desc %u: obs_teams must be 0..7", i);
     return HASE_OK;
 }
+
+namespace hase {
+// The checks hase_create makes of one descriptor (for callers that queue
+// descriptors before any handle exists, such as the rollout server).
+hase_status validate_desc(const hase_env_desc& d, char* msg, size_t n) {
+    const hase_status s = validate(d, 0);
+    if (msg && n) snprintf(msg, n, "%s", g_create_err.c_str());
+    return s;
+}
+}  // namespace hase
 
 // CTA grouping.  Envs are ordered by their kernel-relevant shape (row width,
 // cell packing, radii, emitting teams, agent and seeker counts) so that every group is
@@ -299,7 +309,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if (cfg->n_desc != 1 && cfg->n_desc != cfg->n_envs)
         return fail(nullptr, HASE_EINVAL, "n_desc must be 1 or n_envs");
     if (cfg->ring_steps < 1) return fail(nullptr, HASE_EINVAL, "ring_steps must be >= 1");
-    if ((uint64_t)cfg->env_id_base + cfg->n_envs > 0x100000000ull)
+    if (!cfg->env_ids && (uint64_t)cfg->env_id_base + cfg->n_envs > 0x100000000ull)
         return fail(nullptr, HASE_EINVAL, "env ids exceed 32 bits");
     if (cfg->flags & ~(HASE_EXPORT_ACTIONS | HASE_EXPORT_UNPACKED | HASE_ASYNC_CREATE | HASE_POOL_ALLOC |
                        HASE_DESYNC_START | HASE_EXPORT_CENTRAL | HASE_EXPORT_STATE | HASE_SKIP_OBS |
@@ -338,6 +348,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
 
     h->env.resize(h->n_envs);
     h->thr.resize(h->n_envs);
+    h->keys.resize(h->n_envs);
     h->agent_off.assign(h->n_envs + 1, 0);
     h->obs_off.assign(h->n_envs + 1, 0);
     h->unp_off.assign(h->n_envs + 1, 0);
@@ -368,9 +379,11 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
         E.obs_off = (uint32_t)h->obs_off[e];
         E.unp_off = (uint32_t)h->unp_off[e];
         E.rows_off = (uint32_t)rows;
-        E.env_id = cfg->env_id_base + e;
+        E.env_id = cfg->env_ids ? cfg->env_ids[e] : cfg->env_id_base + e;
         h->env[e] = E;
         h->thr[e] = d.density_thr;
+        const uint64_t sd = cfg->env_seeds ? cfg->env_seeds[e] : cfg->seed;
+        h->keys[e] = make_uint2((uint32_t)(sd & 0xffffffffu), (uint32_t)(sd >> 32));
         h->agent_off[e + 1] = h->agent_off[e] + d.n_agents;
         h->obs_off[e + 1] = h->obs_off[e] + (uint64_t)n_obs * 3 * wmax;
         h->unp_off[e + 1] = h->unp_off[e] + unp;
@@ -476,6 +489,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     }
     HASE_ALLOC(h->d_err, 4);
     HASE_ALLOC(h->d_thr, 4 * h->n_envs);
+    HASE_ALLOC(h->d_keys, sizeof(uint2) * h->n_envs);
     HASE_ALLOC(h->d_clock, 8);
     HASE_ALLOC(h->d_scratch, 8 * 3 * kDigestBlocks);
 #undef HASE_ALLOC
@@ -497,6 +511,10 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
                                     cudaMemcpyHostToDevice, st), "copy env")) != HASE_OK) return s;
     if ((s = finish(cudaMemcpyAsync(h->d_thr, h->thr.data(), 4 * h->n_envs, cudaMemcpyHostToDevice, st),
                     "copy thresholds")) != HASE_OK) return s;
+    if ((s = finish(cudaMemcpyAsync(h->d_keys, h->keys.data(), sizeof(uint2) * h->n_envs, cudaMemcpyHostToDevice,
+                                    st),
+                    "copy keys")) != HASE_OK)
+        return s;
     if ((s = finish(cudaMemcpyAsync(h->d_env_list, h->env_list.data(), 4 * h->n_envs, cudaMemcpyHostToDevice, st),
                     "copy env list")) != HASE_OK) return s;
     if ((s = finish(cudaMemcpyAsync(h->d_groups, h->groups.data(), sizeof(Group) * h->groups.size(),
@@ -504,10 +522,9 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     // episode clocks: 0, or the desynchronised start offsets
     h->est0.assign(h->n_envs, EnvState{0u, 0u});
     if (h->flags & HASE_DESYNC_START) {
-        const uint32_t k0 = (uint32_t)(h->seed & 0xffffffffu), k1 = (uint32_t)(h->seed >> 32);
         for (uint32_t e = 0; e < h->n_envs; ++e) {
             uint32_t c0 = 0u, c1 = 0u, c2 = h->env[e].env_id, c3 = 3u;
-            philox4x32_10(c0, c1, c2, c3, k0, k1);
+            philox4x32_10(c0, c1, c2, c3, h->keys[e].x, h->keys[e].y);
             h->est0[e].ep_t = (uint32_t)(((uint64_t)c0 * h->env[e].cap) >> 32);
         }
     }
@@ -535,8 +552,7 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
                         "copy fog offsets")) != HASE_OK)
             return s;
     }
-    const uint32_t key0 = (uint32_t)(h->seed & 0xffffffffu), key1 = (uint32_t)(h->seed >> 32);
-    if ((s = finish(launch_generate(h->d_env, h->d_thr, h->n_envs, key0, key1, h->d_pos, h->d_start, h->d_rows,
+    if ((s = finish(launch_generate(h->d_env, h->d_thr, h->n_envs, h->d_keys, h->d_pos, h->d_start, h->d_rows,
                                     h->d_err, st), "generate")) != HASE_OK)
         return s;
     const uint64_t last = R - 1;
@@ -653,6 +669,7 @@ static hase_status enqueue_steps(hase_handle* h, uint32_t n_steps, cudaStream_t 
         p.kc = h->kc;
         p.key0 = (uint32_t)(h->seed & 0xffffffffu);
         p.key1 = (uint32_t)(h->seed >> 32);
+        p.keys = h->d_keys;
         p.err = h->d_err;
         for (const auto& F : h->fams) {
             p.groups = h->d_groups + F.first;
@@ -887,10 +904,39 @@ hase_status hase_sync(hase_handle* h) {
     return HASE_OK;
 }
 
-// Partial-sum count of a digest over n_steps steps of h.
-static uint32_t digest_parts(const hase_handle* h, uint32_t n_steps) {
-    const uint64_t total = (uint64_t)n_steps * std::max<uint64_t>(h->obs_words, h->agents);
-    return (uint32_t)std::min<uint64_t>(kDigestBlocks, std::max<uint64_t>(1, (total + 255) / 256));
+// The digest of steps [first, first + n) of envs [e0, e0 + ne): spans of
+// the obs words, done bytes and rewards of one slot, and the partial-sum
+// count of its first pass.
+struct DigestJob {
+    DigestSpan ow, ev, ag;
+    uint64_t first;
+    uint32_t n_steps, n_part;
+};
+
+static hase_status digest_job(hase_handle* h, uint64_t first, uint32_t n_steps, uint32_t e0, uint32_t ne,
+                              DigestJob& J) {
+    if (n_steps < 1 || first + n_steps > h->t || h->t - first > h->ring)
+        return fail(h, HASE_EINVAL, "steps [%llu, %llu) are not all in the ring (steps taken %llu, ring %u)",
+                    (unsigned long long)first, (unsigned long long)(first + n_steps), (unsigned long long)h->t,
+                    h->ring);
+    if (ne < 1 || (uint64_t)e0 + ne > h->n_envs)
+        return fail(h, HASE_EINVAL, "env range [%u, %llu) outside 0..%u", e0, (unsigned long long)e0 + ne, h->n_envs);
+    J.ow = DigestSpan{h->obs_words, h->obs_off[e0], h->obs_off[e0 + ne] - h->obs_off[e0]};
+    J.ev = DigestSpan{h->n_envs, e0, ne};
+    J.ag = DigestSpan{h->agents, h->agent_off[e0], h->agent_off[e0 + ne] - h->agent_off[e0]};
+    J.first = first;
+    J.n_steps = n_steps;
+    const uint64_t total = (uint64_t)n_steps * std::max<uint64_t>(J.ow.count, J.ag.count);
+    J.n_part = (uint32_t)std::min<uint64_t>(kDigestBlocks, std::max<uint64_t>(1, (total + 255) / 256));
+    return HASE_OK;
+}
+
+static hase_status run_digest(hase_handle* h, const DigestJob& J, uint64_t* scratch, hase_digest_out* out,
+                              int64_t* agent_rew, cudaStream_t st) {
+    h->last_stream = st;
+    HASE_CUDA(h, launch_digest(h->d_obs, h->d_done, h->d_rew, J.ow, J.ev, J.ag, h->ring, J.first, J.n_steps, scratch,
+                               J.n_part, h->d_err, reinterpret_cast<uint64_t*>(out), agent_rew, st));
+    return HASE_OK;
 }
 
 hase_status hase_digest_noalloc(hase_handle* h, uint32_t n_steps, hase_digest_out* out, int64_t* agent_rew,
@@ -911,18 +957,15 @@ hase_status hase_digest_noalloc(hase_handle* h, uint32_t n_steps, hase_digest_ou
         std::lock_guard<std::mutex> lock(mu);
         if (!addr[dev]) HASE_CUDA(h, digest_scratch_address(&addr[dev], &words[dev]));
     }
-    // digest_parts caps the first pass at kDigestBlocks blocks, which stride
-    // over the outputs: every digest fits the array (a consistency check)
-    const uint32_t n_part = digest_parts(h, n_steps);
-    if ((uint64_t)3 * n_part > words[dev])
-        return fail(h, HASE_ECUDA, "internal: %u partial sums exceed the static scratch (%zu)", n_part,
+    DigestJob J;
+    hase_status s = digest_job(h, h->t - n_steps, n_steps, 0, h->n_envs, J);
+    if (s != HASE_OK) return s;
+    // the first pass runs at most kDigestBlocks blocks, which stride over the
+    // outputs: every digest fits the array (a consistency check)
+    if ((uint64_t)3 * J.n_part > words[dev])
+        return fail(h, HASE_ECUDA, "internal: %u partial sums exceed the static scratch (%zu)", J.n_part,
                     words[dev] / 3);
-    cudaStream_t st = (cudaStream_t)stream;
-    h->last_stream = st;
-    HASE_CUDA(h, launch_digest(h->d_obs, h->d_done, h->d_rew, h->obs_words, h->n_envs, h->agents, h->ring,
-                               h->t - n_steps, n_steps, addr[dev], n_part, h->d_err,
-                               reinterpret_cast<uint64_t*>(out), agent_rew, st));
-    return HASE_OK;
+    return run_digest(h, J, addr[dev], out, agent_rew, (cudaStream_t)stream);
 }
 
 hase_status hase_digest(hase_handle* h, uint32_t n_steps, hase_digest_out* out, int64_t* agent_rew,
@@ -931,13 +974,20 @@ hase_status hase_digest(hase_handle* h, uint32_t n_steps, hase_digest_out* out, 
     if (!out) return fail(h, HASE_EINVAL, "out is NULL");
     if (n_steps < 1 || n_steps > h->ring || n_steps > h->t)
         return fail(h, HASE_EINVAL, "n_steps must be in 1..min(ring_steps, steps taken)");
-    cudaStream_t st = (cudaStream_t)stream;
-    h->last_stream = st;
-    const uint32_t n_part = digest_parts(h, n_steps);
-    HASE_CUDA(h, launch_digest(h->d_obs, h->d_done, h->d_rew, h->obs_words, h->n_envs, h->agents, h->ring,
-                               h->t - n_steps, n_steps, h->d_scratch, n_part, h->d_err,
-                               reinterpret_cast<uint64_t*>(out), agent_rew, st));
-    return HASE_OK;
+    DigestJob J;
+    hase_status s = digest_job(h, h->t - n_steps, n_steps, 0, h->n_envs, J);
+    if (s != HASE_OK) return s;
+    return run_digest(h, J, h->d_scratch, out, agent_rew, (cudaStream_t)stream);
+}
+
+hase_status hase_digest_range(hase_handle* h, uint64_t first_step, uint32_t n_steps, uint32_t env_first,
+                              uint32_t env_count, hase_digest_out* out, int64_t* agent_rew, void* stream) {
+    if (!h) return fail(nullptr, HASE_EINVAL, "handle is NULL");
+    if (!out) return fail(h, HASE_EINVAL, "out is NULL");
+    DigestJob J;
+    hase_status s = digest_job(h, first_step, n_steps, env_first, env_count, J);
+    if (s != HASE_OK) return s;
+    return run_digest(h, J, h->d_scratch, out, agent_rew, (cudaStream_t)stream);
 }
 
 hase_status hase_launch_info(hase_handle* h, uint32_t* ctas, uint32_t* threads, uint32_t* smem,

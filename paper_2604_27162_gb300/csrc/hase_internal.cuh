@@ -331,6 +331,12 @@ __host__ __device__ inline void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32
     }
 }
 
+// Entries [first, first + count) of every ring slot of `stride` entries
+// (run digests over the whole batch or over one env range).
+struct DigestSpan {
+    uint64_t stride, first, count;
+};
+
 struct StepParams {
     const EnvRT* env;
     EnvState* est;
@@ -364,7 +370,8 @@ struct StepParams {
     uint32_t kc;         // steps per chunk (<= kMaxChunk, <= ring)
     uint32_t n_dyn;      // dynamics warps per CTA (the largest group's)
     uint32_t emit_warps;
-    uint32_t key0, key1;
+    uint32_t key0, key1;        // (unused by the kernels: every env has its own key in `keys`)
+    const uint2* keys;          // per env: Philox key (seed & 0xffffffff, seed >> 32)
     uint32_t dyn_ids;           // streaming form: warp id of dynamics warp d in bits [4d, 4d + 4),
                                 // of the action warp in bits [16, 20)
     uint32_t* err;              // error word (kErrWaitTimeout)

@@ -19,7 +19,7 @@ namespace hase {
 // a0: generation.  One warp per env.
 // --------------------------------------------------------------------------
 __global__ void gen_kernel(const EnvRT* __restrict__ env, const uint32_t* __restrict__ thr,
-                           uint32_t n_envs, uint32_t key0, uint32_t key1, uint16_t* __restrict__ pos,
+                           uint32_t n_envs, const uint2* __restrict__ keys, uint16_t* __restrict__ pos,
                            uint16_t* __restrict__ start, uint64_t* __restrict__ rows,
                            uint32_t* __restrict__ err) {
     const uint32_t e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -27,6 +27,7 @@ __global__ void gen_kernel(const EnvRT* __restrict__ env, const uint32_t* __rest
     if (e >= n_envs) return;
     const EnvRT E = env[e];
     const uint32_t density_thr = thr[e];
+    const uint32_t key0 = keys[e].x, key1 = keys[e].y;  // the env's Philox key
     const int S = E.side, A = E.n_agents, rw = E.rw;
     // start cells: agent a draws word 0 of counter (attempt, a, env, 2),
     // redrawing while the cell is taken by an earlier agent.  Lane 0 alone.
@@ -212,12 +213,11 @@ cudaError_t launch_fog_init(const EnvRT* env, uint32_t n_envs, const uint16_t* p
 // --------------------------------------------------------------------------
 // Launchers (host).
 // --------------------------------------------------------------------------
-cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_envs, uint32_t key0,
-                            uint32_t key1, uint16_t* pos, uint16_t* start, uint64_t* rows, uint32_t* err,
-                            cudaStream_t st) {
+cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_envs, const uint2* keys,
+                            uint16_t* pos, uint16_t* start, uint64_t* rows, uint32_t* err, cudaStream_t st) {
     if (n_envs == 0) return cudaSuccess;
     const uint32_t wpb = 4;
-    gen_kernel<<<(n_envs + wpb - 1) / wpb, wpb * 32, 0, st>>>(env, thr, n_envs, key0, key1, pos, start,
+    gen_kernel<<<(n_envs + wpb - 1) / wpb, wpb * 32, 0, st>>>(env, thr, n_envs, keys, pos, start,
                                                               rows, err);
     return cudaGetLastError();
 }
@@ -230,10 +230,12 @@ cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* po
 }
 
 // --------------------------------------------------------------------------
-// Run digest: order-independent sums (mod 2^64) over the ring slots of the
-// last n steps.  Pass 1: every block reduces a grid-stride share of the obs
-// words, done bytes and rewards into scratch[block] (three words); pass 2: one
-// block adds the partials.  A third kernel gives per-agent reward sums.
+// Run digest: order-independent sums (mod 2^64) over the ring slots of n
+// consecutive steps, of one span (stride, first, count) per slot of the obs
+// words, the done bytes and the rewards (the whole slot, or one env range).
+// Pass 1: every block reduces a grid-stride share of the obs words, done
+// bytes and rewards into scratch[block] (three words); pass 2: one block adds
+// the partials.  A third kernel gives per-agent reward sums.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
     z += 0x9E3779B97F4A7C15ull;
@@ -275,31 +277,31 @@ struct Walk {
     }
 };
 
-__global__ void digest_partial_kernel(const uint64_t* obs, const uint8_t* done, const int32_t* rew,
-                                      uint64_t obs_words, uint64_t n_envs, uint64_t agents, uint32_t ring,
-                                      uint64_t first, uint32_t n_steps, uint64_t* scratch) {
+__global__ void digest_partial_kernel(const uint64_t* obs, const uint8_t* done, const int32_t* rew, DigestSpan ow,
+                                      DigestSpan ev, DigestSpan ag, uint32_t ring, uint64_t first, uint32_t n_steps,
+                                      uint64_t* scratch) {
     __shared__ uint64_t red[32];
     const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t dig = 0, eps = 0, rs = 0;
-    if (obs_words) {
-        const uint64_t total = (uint64_t)n_steps * obs_words;
-        Walk w(i0, obs_words);
-        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(obs_words)) {
+    if (ow.count) {  // digest index of word j of step s: s * count + j
+        const uint64_t total = (uint64_t)n_steps * ow.count;
+        Walk w(i0, ow.count);
+        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(ow.count)) {
             const uint64_t slot = (first + w.s) % ring;
-            dig += splitmix64(obs[slot * obs_words + w.j] ^ i);
+            dig += splitmix64(obs[slot * ow.stride + ow.first + w.j] ^ i);
         }
     }
-    {
-        const uint64_t total = (uint64_t)n_steps * n_envs;
-        Walk w(i0, n_envs);
-        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(n_envs))
-            eps += done[((first + w.s) % ring) * n_envs + w.j] & 1u;
+    if (ev.count) {
+        const uint64_t total = (uint64_t)n_steps * ev.count;
+        Walk w(i0, ev.count);
+        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(ev.count))
+            eps += done[((first + w.s) % ring) * ev.stride + ev.first + w.j] & 1u;
     }
-    {
-        const uint64_t total = (uint64_t)n_steps * agents;
-        Walk w(i0, agents);
-        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(agents))
-            rs += (uint64_t)(int64_t)rew[((first + w.s) % ring) * agents + w.j];
+    if (ag.count) {
+        const uint64_t total = (uint64_t)n_steps * ag.count;
+        Walk w(i0, ag.count);
+        for (uint64_t i = i0; i < total; i += (uint64_t)gridDim.x * blockDim.x, w.next(ag.count))
+            rs += (uint64_t)(int64_t)rew[((first + w.s) % ring) * ag.stride + ag.first + w.j];
     }
     dig = block_sum(dig, red);
     eps = block_sum(eps, red);
@@ -325,12 +327,12 @@ __global__ void digest_final_kernel(const uint64_t* scratch, uint32_t n_part, co
     }
 }
 
-__global__ void agent_reward_kernel(const int32_t* rew, uint64_t agents, uint32_t ring, uint64_t first,
+__global__ void agent_reward_kernel(const int32_t* rew, DigestSpan ag, uint32_t ring, uint64_t first,
                                     uint32_t n_steps, int64_t* agent_rew) {
-    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < agents;
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < ag.count;
          a += (uint64_t)gridDim.x * blockDim.x) {
         int64_t s = 0;
-        for (uint32_t k = 0; k < n_steps; ++k) s += rew[((first + k) % ring) * agents + a];
+        for (uint32_t k = 0; k < n_steps; ++k) s += rew[((first + k) % ring) * ag.stride + ag.first + a];
         agent_rew[a] = s;
     }
 }
@@ -345,16 +347,14 @@ cudaError_t digest_scratch_address(uint64_t** p, size_t* words) {
     return cudaGetSymbolAddress(reinterpret_cast<void**>(p), g_digest_scratch);
 }
 
-cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, uint64_t obs_words,
-                          uint64_t n_envs, uint64_t agents, uint32_t ring, uint64_t first, uint32_t n_steps,
-                          uint64_t* scratch, uint32_t n_part, const uint32_t* err, uint64_t* out,
-                          int64_t* agent_rew, cudaStream_t st) {
-    digest_partial_kernel<<<n_part, 256, 0, st>>>(obs, done, rew, obs_words, n_envs, agents, ring, first, n_steps,
-                                                  scratch);
+cudaError_t launch_digest(const uint64_t* obs, const uint8_t* done, const int32_t* rew, DigestSpan ow, DigestSpan ev,
+                          DigestSpan ag, uint32_t ring, uint64_t first, uint32_t n_steps, uint64_t* scratch,
+                          uint32_t n_part, const uint32_t* err, uint64_t* out, int64_t* agent_rew, cudaStream_t st) {
+    digest_partial_kernel<<<n_part, 256, 0, st>>>(obs, done, rew, ow, ev, ag, ring, first, n_steps, scratch);
     digest_final_kernel<<<1, 256, 0, st>>>(scratch, n_part, err, out);
-    if (agent_rew && agents)
-        agent_reward_kernel<<<(uint32_t)std::min<uint64_t>((agents + 255) / 256, 1024), 256, 0, st>>>(
-            rew, agents, ring, first, n_steps, agent_rew);
+    if (agent_rew && ag.count)
+        agent_reward_kernel<<<(uint32_t)std::min<uint64_t>((ag.count + 255) / 256, 1024), 256, 0, st>>>(
+            rew, ag, ring, first, n_steps, agent_rew);
     return cudaGetLastError();
 }
 

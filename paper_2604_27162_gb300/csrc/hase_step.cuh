@@ -408,7 +408,7 @@ struct CtaShared {
     GroupPlan plan;
     SlotRec slot[kMaxGroupSlots];
     uint16_t p0[kMaxGroupSlots];  // pristine start cells (CTA packing)
-    uint2 key[kMaxGroupSlots];     // Philox action counter words (agent, env id)
+    uint4 key[kMaxGroupSlots];     // Philox action counter words (agent, env id) and the env's key
 };
 
 __device__ __forceinline__ uint32_t to_cta(uint32_t p6, uint32_t sh) { return (p6 & 63u) | ((p6 >> 6) << sh); }
@@ -1136,7 +1136,8 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
         const EnvRT& E = H.env[r.env];
         H.slot[sidx].p0 = (uint16_t)to_cta(P.start[E.agent_off + r.agent], cell_shift(E));
         H.p0[sidx] = H.slot[sidx].p0;
-        H.key[sidx] = make_uint2(r.agent, E.env_id);
+        const uint2 k = P.keys[H.gidx[r.env]];
+        H.key[sidx] = make_uint4(r.agent, E.env_id, k.x, k.y);
     }
     __syncthreads();
     // cell state and claims, obstacle-window tables (plane 0 of every cell
@@ -1229,11 +1230,11 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
         for (uint32_t it = (uint32_t)worker; it < n_items; it += stride) {
             const uint32_t it2 = it + (uint32_t)n_workers;
             const bool two = it2 < n_items;
-            const uint2 ka = H.key[it % ns], kb = H.key[(two ? it2 : it) % ns];
+            const uint4 ka = H.key[it % ns], kb = H.key[(two ? it2 : it) % ns];
             uint32_t a0 = (uint32_t)(b0 + it / ns), a1 = ka.x, a2 = ka.y, a3 = 0u;
             uint32_t d0 = (uint32_t)(b0 + (two ? it2 : it) / ns), d1 = kb.x, d2 = kb.y, d3 = 0u;
-            philox4x32_10(a0, a1, a2, a3, P.key0, P.key1);
-            philox4x32_10(d0, d1, d2, d3, P.key0, P.key1);
+            philox4x32_10(a0, a1, a2, a3, ka.z, ka.w);
+            philox4x32_10(d0, d1, d2, d3, kb.z, kb.w);
             put(it, a0, a1, a2, a3);
             if (two) put(it2, d0, d1, d2, d3);
         }

@@ -64,7 +64,7 @@ struct StreamShared {
     GroupPlan plan;
     SlotRec slot[kMaxGroupSlots];
     uint16_t scratch[128 + 2 * 4 * 32 * kMaxDyn];  // dynamics lanes without work: record and byte scratch
-    uint2 key[kMaxGroupSlots];          // Philox action counter words (agent, env id) of every slot
+    uint4 key[kMaxGroupSlots];          // Philox action counter words (agent, env id) and the env's key
     uint32_t act_prog;                  // quads of actions the action warp has drawn (from the launch's first)
     uint32_t dyn_prog[kMaxDyn];         // steps every dynamics warp has recorded
     uint32_t emit_prog[kMaxEmitWarps];  // steps every emission warp has finished reading
@@ -648,7 +648,8 @@ __global__ void __launch_bounds__(MAXT, 1) stream_kernel(const StepParams P) {
         const EnvRT& E = H.env[r.env];
         const uint16_t p0 = (uint16_t)to_cta(P.start[E.agent_off + r.agent], cell_shift(E));
         H.slot[sidx].p0 = p0;
-        H.key[sidx] = make_uint2(r.agent, E.env_id);
+        const uint2 kk = P.keys[H.gidx[r.env]];
+        H.key[sidx] = make_uint4(r.agent, E.env_id, kk.x, kk.y);
         s_prist[r.env * rec16 + r.agent] = p0;
     }
     // state bytes (free neighbours) and window tables
@@ -733,11 +734,11 @@ __global__ void __launch_bounds__(MAXT, 1) stream_kernel(const StepParams P) {
                 const bool two = it2 < items;
                 const uint32_t ja = it / ns, sa = it - ja * ns;
                 const uint32_t jb = two ? it2 / ns : ja, sb = two ? it2 - jb * ns : sa;
-                const uint2 ka = H.key[sa], kb = H.key[sb];
+                const uint4 ka = H.key[sa], kb = H.key[sb];
                 uint32_t a0 = q0 + r0 + ja, a1 = ka.x, a2 = ka.y, a3 = 0u;
                 uint32_t b0 = q0 + r0 + jb, b1 = kb.x, b2 = kb.y, b3 = 0u;
-                philox4x32_10(a0, a1, a2, a3, P.key0, P.key1);
-                philox4x32_10(b0, b1, b2, b3, P.key0, P.key1);
+                philox4x32_10(a0, a1, a2, a3, ka.z, ka.w);
+                philox4x32_10(b0, b1, b2, b3, kb.z, kb.w);
                 const uint32_t wa = mulhi_n(a0, 5u) | (mulhi_n(a1, 5u) << 8) | (mulhi_n(a2, 5u) << 16) |
                                     (mulhi_n(a3, 5u) << 24);
                 const uint32_t wb = mulhi_n(b0, 5u) | (mulhi_n(b1, 5u) << 8) | (mulhi_n(b2, 5u) << 16) |

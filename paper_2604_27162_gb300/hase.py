@@ -41,11 +41,13 @@ STATUS_NAMES = {0: "HASE_OK", 1: "HASE_EINVAL", 2: "HASE_ENOMEM", 3: "HASE_ECUDA
 
 # Every symbol include/hase.h declares (the CPU tests check the export list).
 EXPORTS = [
-    "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_digest", "hase_digest_noalloc",
+    "hase_create", "hase_reset", "hase_step", "hase_step_graph", "hase_digest", "hase_digest_range",
+    "hase_digest_noalloc",
     "hase_obs_ptr", "hase_reward_ptr", "hase_done_ptr",
     "hase_actions_ptr", "hase_central_ptr", "hase_state_ptr", "hase_fog_ptr", "hase_layout_get", "hase_step_count", "hase_get_state", "hase_set_state",
     "hase_get_world", "hase_sync", "hase_launch_info", "hase_destroy", "hase_last_error",
-    "hase_request_bytes", "hase_serve",
+    "hase_request_bytes", "hase_serve", "hase_server_create", "hase_server_submit", "hase_server_poll",
+    "hase_server_stats", "hase_server_shutdown", "hase_server_destroy",
 ]
 
 
@@ -74,6 +76,8 @@ class hase_config(C.Structure):
         ("emit_warps", C.c_uint32),
         ("max_group_envs", C.c_uint32),
         ("smem_cap", C.c_uint32),
+        ("env_seeds", C.POINTER(C.c_uint64)),
+        ("env_ids", C.POINTER(C.c_uint32)),
     ]
 
 
@@ -103,11 +107,26 @@ class hase_serve_config(C.Structure):
         ("n_streams", C.c_uint32),
         ("max_inflight", C.c_uint32),
         ("time_scale", C.c_double),
+        ("max_batch", C.c_uint32),
+        ("pad", C.c_uint32),
+    ]
+
+
+class hase_server_config(C.Structure):
+    _fields_ = [
+        ("budget_bytes", C.c_uint64),
+        ("n_streams", C.c_uint32),
+        ("max_inflight", C.c_uint32),
+        ("queue_capacity", C.c_uint32),
+        ("max_batch_envs", C.c_uint32),
+        ("max_batch", C.c_uint32),
+        ("pad", C.c_uint32),
     ]
 
 
 class hase_request_result(C.Structure):
     _fields_ = [
+        ("submitted", C.c_double),
         ("admitted", C.c_double),
         ("finished", C.c_double),
         ("digest", C.c_uint64),
@@ -115,7 +134,7 @@ class hase_request_result(C.Structure):
         ("reward_sum", C.c_int64),
         ("bytes", C.c_uint64),
         ("status", C.c_uint32),
-        ("pad", C.c_uint32),
+        ("batch_size", C.c_uint32),
     ]
 
 
@@ -125,6 +144,8 @@ class hase_serve_stats(C.Structure):
         ("peak_bytes", C.c_uint64),
         ("peak_inflight", C.c_uint32),
         ("rejected", C.c_uint32),
+        ("batches", C.c_uint64),
+        ("requests", C.c_uint64),
     ]
 
 
@@ -165,7 +186,15 @@ def load(path=LIB_PATH):
     L.hase_step_graph.argtypes = [H, u32, P]
     L.hase_digest.argtypes = [H, u32, P, P, P]
     L.hase_digest_noalloc.argtypes = [H, u32, P, P, P]
+    L.hase_digest_range.argtypes = [H, u64, u32, u32, u32, P, P, P]
     L.hase_request_bytes.argtypes = [C.POINTER(hase_request)]
+    L.hase_server_create.argtypes = [C.POINTER(hase_server_config), C.POINTER(P)]
+    L.hase_server_submit.argtypes = [P, C.POINTER(hase_request), C.POINTER(u64)]
+    L.hase_server_poll.argtypes = [P, u64, C.c_double, C.POINTER(hase_request_result)]
+    L.hase_server_stats.argtypes = [P, C.POINTER(hase_serve_stats)]
+    L.hase_server_shutdown.argtypes = [P]
+    L.hase_server_destroy.argtypes = [P]
+    L.hase_server_destroy.restype = None
     L.hase_serve.argtypes = [C.POINTER(hase_request), u32, C.POINTER(hase_serve_config),
                              C.POINTER(hase_request_result), C.POINTER(hase_serve_stats)]
     L.hase_obs_ptr.argtypes = [H, C.POINTER(P), C.POINTER(P)]
@@ -212,17 +241,24 @@ def _stream(stream):
 # C names, one to one.
 # ---------------------------------------------------------------------------
 def make_config(n_envs, seed, descs, ring_steps, flags=0, env_id_base=0, steps_per_launch=0,
-                chunk_steps=0, emit_warps=0, max_group_envs=0, smem_cap=0):
+                chunk_steps=0, emit_warps=0, max_group_envs=0, smem_cap=0, env_seeds=None, env_ids=None):
     arr = (hase_env_desc * len(descs))()
     for i, d in enumerate(descs):
         for k, _ in hase_env_desc._fields_:
             setattr(arr[i], k, int(d[k]))
+    seeds = ids = None
+    if env_seeds is not None:
+        seeds = (C.c_uint64 * n_envs)(*[int(v) & (2**64 - 1) for v in env_seeds])
+    if env_ids is not None:
+        ids = (C.c_uint32 * n_envs)(*[int(v) for v in env_ids])
     cfg = hase_config(n_envs=n_envs, env_id_base=env_id_base, seed=seed & (2**64 - 1),
                       envs=C.cast(arr, C.POINTER(hase_env_desc)), n_desc=len(descs),
                       ring_steps=ring_steps, flags=flags, steps_per_launch=steps_per_launch,
                       chunk_steps=chunk_steps, emit_warps=emit_warps, max_group_envs=max_group_envs,
-                      smem_cap=smem_cap)
-    cfg._keep = arr  # keep the descriptor array alive
+                      smem_cap=smem_cap,
+                      env_seeds=C.cast(seeds, C.POINTER(C.c_uint64)) if seeds is not None else None,
+                      env_ids=C.cast(ids, C.POINTER(C.c_uint32)) if ids is not None else None)
+    cfg._keep = (arr, seeds, ids)  # keep the host arrays alive
     return cfg
 
 
@@ -267,20 +303,77 @@ def hase_request_bytes(r):
     return int(load().hase_request_bytes(C.byref(_requests([r])[0])))
 
 
-def hase_serve(reqs, budget_bytes, n_streams=16, max_inflight=1024, time_scale=1.0):
+def hase_serve(reqs, budget_bytes, n_streams=16, max_inflight=1024, time_scale=1.0, max_batch=0):
     """Serve the request list (dicts with arrival, seed, n_envs, steps, desc)
     and return (per-request result dicts, stats dict)."""
     arr = _requests(reqs)
     cfg = hase_serve_config(budget_bytes=int(budget_bytes), n_streams=n_streams, max_inflight=max_inflight,
-                            time_scale=float(time_scale))
+                            time_scale=float(time_scale), max_batch=max_batch)
     res = (hase_request_result * max(1, len(reqs)))()
     stats = hase_serve_stats()
     status = load().hase_serve(arr, len(reqs), C.byref(cfg), res, C.byref(stats))
     if status != HASE_OK:
         raise HaseError(status, "hase_serve failed")
-    out = [{k: getattr(res[i], k) for k, _ in hase_request_result._fields_ if k != "pad"}
-           for i in range(len(reqs))]
+    out = [{k: getattr(res[i], k) for k, _ in hase_request_result._fields_} for i in range(len(reqs))]
     return out, {k: getattr(stats, k) for k, _ in hase_serve_stats._fields_}
+
+
+class Server:
+    """A rollout server (hase_server_*): submit from any thread, poll by id."""
+
+    def __init__(self, budget_bytes, n_streams=16, max_inflight=4096, queue_capacity=65536, max_batch_envs=0,
+                 max_batch=0):
+        cfg = hase_server_config(budget_bytes=int(budget_bytes), n_streams=n_streams, max_inflight=max_inflight,
+                                 queue_capacity=queue_capacity, max_batch_envs=max_batch_envs, max_batch=max_batch)
+        self.s = C.c_void_p()
+        status = load().hase_server_create(C.byref(cfg), C.byref(self.s))
+        if status != HASE_OK:
+            raise HaseError(status, "hase_server_create failed")
+
+    def submit(self, req):
+        """Queue one request dict; returns its id (HaseError: HASE_EBUSY, HASE_ESTATE, HASE_EINVAL)."""
+        rid = C.c_uint64()
+        status = load().hase_server_submit(self.s, C.byref(_requests([dict(req, arrival=0.0)])[0]), C.byref(rid))
+        if status != HASE_OK:
+            raise HaseError(status, "hase_server_submit failed")
+        return rid.value
+
+    def poll(self, rid, timeout_s=0.0):
+        """The result dict of request rid, or None when it has not finished within timeout_s."""
+        res = hase_request_result()
+        status = load().hase_server_poll(self.s, rid, float(timeout_s), C.byref(res))
+        if status == HASE_ETIMEOUT:
+            return None
+        if status != HASE_OK:
+            raise HaseError(status, "hase_server_poll failed")
+        return {k: getattr(res, k) for k, _ in hase_request_result._fields_}
+
+    def stats(self):
+        st = hase_serve_stats()
+        load().hase_server_stats(self.s, C.byref(st))
+        return {k: getattr(st, k) for k, _ in hase_serve_stats._fields_}
+
+    def shutdown(self):
+        status = load().hase_server_shutdown(self.s)
+        if status != HASE_OK:
+            raise HaseError(status, "hase_server_shutdown failed")
+
+    def close(self):
+        if self.s:
+            load().hase_server_destroy(self.s)
+            self.s = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hase_digest_range(h, first_step, n_steps, env_first, env_count, out_ptr, agent_rew_ptr=None, stream=None):
+    """hase_digest of steps [first_step, first_step + n_steps) of an env range."""
+    _check(load().hase_digest_range(h, C.c_uint64(first_step), n_steps, env_first, env_count, C.c_void_p(out_ptr),
+                                    C.c_void_p(agent_rew_ptr or 0), _stream(stream)), h)
 
 
 def hase_digest_noalloc(h, n_steps, out_ptr, agent_rew_ptr=None, stream=None):

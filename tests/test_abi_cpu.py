@@ -33,17 +33,27 @@ def test_library_exports_every_declared_symbol():
     assert sorted(hase.EXPORTS) == names
 
 
-def test_binding_struct_sizes_match_header():
+def test_binding_struct_sizes_match_header(tmp_path):
+    """Every struct of the binding has the size the C compiler gives the
+    header's declaration."""
+    import os
+    import subprocess
+
     from paper_2604_27162_gb300 import hase
 
-    assert ctypes.sizeof(hase.hase_env_desc) == 32
-    assert ctypes.sizeof(hase.hase_config) == 56
-    assert ctypes.sizeof(hase.hase_layout) == 88
-    assert ctypes.sizeof(hase.hase_digest_out) == 32
-    assert ctypes.sizeof(hase.hase_request) == 56
-    assert ctypes.sizeof(hase.hase_serve_config) == 24
-    assert ctypes.sizeof(hase.hase_request_result) == 56
-    assert ctypes.sizeof(hase.hase_serve_stats) == 24
+    structs = [n for n in dir(hase) if n.startswith("hase_") and isinstance(getattr(hase, n), type)
+               and issubclass(getattr(hase, n), ctypes.Structure)]
+    assert "hase_config" in structs and "hase_server_config" in structs
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include "hase.h"\n#include "hase_serve.h"\nint main(void) {\n'
+                   + "".join('    printf("%%s %%zu\\n", "%s", sizeof(%s));\n' % (n, n) for n in structs)
+                   + "    return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for n in structs:
+        assert ctypes.sizeof(getattr(hase, n)) == int(got[n]), n
 
 
 def test_missing_library_fails_loudly(tmp_path):

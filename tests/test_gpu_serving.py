@@ -100,3 +100,81 @@ def test_serving_respects_budget_and_rejects_oversize():
     for i in (0, 5, 17):
         ref = _oracle_digest(reqs[i])
         assert res[i]["digest"] == ref["digest"]
+
+
+def test_server_shared_batches_equal_oracle_and_alone():
+    """Requests submitted from two threads while the server runs share
+    batches (one handle, every step launch) and still give the oracle's
+    result of each request run alone."""
+    import threading
+
+    reqs = small_requests(60, seed=11)
+    budget = 4 * sum(hase.hase_request_bytes(r) for r in reqs)
+    srv = hase.Server(budget, n_streams=4, max_inflight=256)
+    ids = [None] * len(reqs)
+
+    def submit(part):
+        for i in part:
+            ids[i] = srv.submit(reqs[i])
+
+    threads = [threading.Thread(target=submit, args=(range(k, len(reqs), 2),)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    res = [srv.poll(rid, timeout_s=60.0) for rid in ids]
+    stats = srv.stats()
+    srv.shutdown()
+    srv.close()
+    assert all(r is not None and r["status"] == hase.HASE_OK for r in res)
+    assert stats["requests"] == len(reqs) and stats["batches"] < len(reqs)
+    assert max(r["batch_size"] for r in res) > 1, "no request shared a batch"
+    for i in range(0, len(reqs), 6):
+        ref = _oracle_digest(reqs[i])
+        assert (res[i]["digest"], res[i]["episodes"], res[i]["reward_sum"]) == (
+            ref["digest"], ref["episodes"], int(ref["reward_sum"].sum())), i
+        assert res[i]["finished"] >= res[i]["admitted"] >= res[i]["submitted"]
+    alone = hase.Server(budget, n_streams=1, max_batch=1)  # every request its own handle
+    for i in (1, 8, 33):
+        r1 = alone.poll(alone.submit(reqs[i]), timeout_s=60.0)
+        assert r1["batch_size"] == 1
+        for k in ("digest", "episodes", "reward_sum", "status"):
+            assert r1[k] == res[i][k], (i, k)
+    alone.close()
+
+
+def test_server_status_codes():
+    reqs = small_requests(8, seed=12)
+    long = dict(reqs[0], n_envs=2000, steps=4000)
+    budget = int(hase.hase_request_bytes(long) * 1.2)
+    srv = hase.Server(budget, n_streams=1, max_inflight=4, queue_capacity=1)
+    import time
+
+    first = srv.submit(long)
+    assert srv.poll(first, timeout_s=0.0) is None  # HASE_ETIMEOUT: not finished yet
+    t = time.time()
+    while srv.stats()["peak_inflight"] < 1:  # admitted (requests under admission count as queued)
+        assert time.time() - t < 30
+        time.sleep(1e-3)
+    srv.submit(dict(long, seed=5))  # waits in the queue for memory
+    busy = 0
+    for r in reqs[1:]:
+        try:
+            srv.submit(r)
+        except hase.HaseError as e:
+            assert e.status == hase.HASE_EBUSY
+            busy += 1
+    assert busy > 0, "the one-slot queue never filled"
+    with pytest.raises(hase.HaseError) as ei:  # an invalid request
+        srv.submit(dict(reqs[1], desc=dict(reqs[1]["desc"], side=99)))
+    assert ei.value.status == hase.HASE_EINVAL
+    big = srv.submit(dict(long, n_envs=4000, steps=8000))  # never fits: finished at once
+    assert srv.poll(big, timeout_s=1.0)["status"] == hase.HASE_ENOMEM
+    with pytest.raises(hase.HaseError):
+        srv.poll(big)  # already collected
+    assert srv.poll(first, timeout_s=120.0)["status"] == hase.HASE_OK
+    srv.shutdown()  # finishes the queued request
+    with pytest.raises(hase.HaseError) as ei:
+        srv.submit(reqs[2])
+    assert ei.value.status == hase.HASE_ESTATE
+    srv.close()
