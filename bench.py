@@ -148,6 +148,68 @@ def peaks():
         return 6800.0, "fallback"
 
 
+class NvmlSampler:
+    """SM clock, power and clock-event reasons read through NVML (ctypes,
+    read-only queries) every `period` seconds in a background thread."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, gpu_index, period=0.002):
+        import ctypes
+
+        self.gpu, self.period = gpu_index, period
+        self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.rows, self.stop_flag, self.thread = [], False, None
+
+    def _read(self):
+        import ctypes
+
+        mhz, mx, mw = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint()
+        reasons = ctypes.c_ulonglong()
+        self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(mhz))  # NVML_CLOCK_SM
+        self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx))
+        self.nv.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(mw))
+        self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h, ctypes.byref(reasons))
+        return mhz.value, mx.value, mw.value / 1e3, reasons.value
+
+    def start(self):
+        import threading
+
+        def loop():
+            while not self.stop_flag:
+                self.rows.append(self._read())
+                time.sleep(self.period)
+
+        self.rows.append(self._read())
+        self.thread = threading.Thread(target=loop, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag = True
+        if self.thread:
+            self.thread.join()
+        self.rows.append(self._read())
+        sm = [r[0] for r in self.rows]
+        reasons = sorted({name for r in self.rows for bit, name in self.REASONS.items() if r[3] & bit})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in self.rows), "reasons": reasons,
+                "samples": len(self.rows), "power_w_max": max(r[2] for r in self.rows), "source": "nvml",
+                "period_ms": self.period * 1e3}
+
+
+def clock_sampler(gpu_index):
+    """NVML sampling when the library is there, else nvidia-smi."""
+    try:
+        return NvmlSampler(gpu_index)
+    except Exception:
+        return ClockSampler(gpu_index)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -167,7 +229,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -196,7 +258,7 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "source": "nvidia-smi"}
 
 
 def issue_roofline(inst_per_env_step, env_steps_per_s, clk):
@@ -319,13 +381,13 @@ def run_gpu(args):
     eng = engines[0]
     info = eng.launch_info()
 
+    clocks = clock_sampler(local)  # from the warm-up on, through the timed region
+    clocks.start()
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -434,38 +496,79 @@ def engine_exports(eng):
 
 
 def run_e2e(eng, c, run, stream, args):
+    """The rollout through the public API with every step's outputs copied to
+    pinned host memory inside the timed region: the steps of chunk k + 1 run
+    on the compute stream while chunk k's slots are copied on a second stream
+    (events order them; a chunk's slots are stepped again only after their
+    copy).  Beside it: the pinned device-to-host copy rate of the same chunk
+    bytes alone, the link's measured peak for this traffic."""
     import torch
 
     n_steps = run * max(1, min(args.steps, 3))
     ex = engine_exports(eng)
     per_step = sum(v.shape[1] * v.element_size() for _, v in ex)
-    chunk = max(1, min(1000, run, (1 << 30) // per_step))  # pinned staging of at most 1 GiB
-    host = [torch.empty((chunk, v.shape[1]), dtype=v.dtype, pin_memory=True) for _, v in ex]
+    chunk = max(1, min(1000, run, (1 << 30) // per_step))  # pinned staging of at most 1 GiB a buffer
+    host = [[torch.empty((chunk, v.shape[1]), dtype=v.dtype, pin_memory=True) for _, v in ex] for _ in range(2)]
+    copy = torch.cuda.Stream()
+    done_copy = {}  # ring chunk index -> event after its copy
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    done_steps = 0
+    done_steps, k = 0, 0
     while done_steps < n_steps:
         n = min(chunk, n_steps - done_steps)
-        s = eng.t % eng.ring
+        s0 = eng.t % eng.ring
+        idx = [(s0 + i) % eng.ring for i in range(n)]
+        for sl in {i // chunk for i in idx}:  # the slots' previous copy must be done
+            if sl in done_copy:
+                stream.wait_event(done_copy[sl])
         eng.step(n)
-        idx = [(s + i) % eng.ring for i in range(n)]
-        lo = idx[0]
-        for (_, v), hb in zip(ex, host):
-            if lo + n <= eng.ring:
-                hb[:n].copy_(v[lo:lo + n], non_blocking=True)
-            else:
-                for j, sl in enumerate(idx):
-                    hb[j].copy_(v[sl], non_blocking=True)
+        stepped = torch.cuda.Event()
+        stepped.record(stream)
+        copy.wait_event(stepped)
+        hb = host[k % 2]
+        with torch.cuda.stream(copy):
+            for (_, v), h in zip(ex, hb):
+                if idx[0] + n <= eng.ring:
+                    h[:n].copy_(v[idx[0]:idx[0] + n], non_blocking=True)
+                else:
+                    for j, sl in enumerate(idx):
+                        h[j].copy_(v[sl], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(copy)
+        for sl in {i // chunk for i in idx}:
+            done_copy[sl] = ev
         done_steps += n
+        k += 1
+    stream.wait_stream(copy)
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
+    # the same bytes copied alone (pinned, one stream): the link's rate for this traffic
+    v0 = ex[0][1]
+    nbytes = chunk * per_step
+    dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    hst = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    for _ in range(2):
+        hst.copy_(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    c0.record()
+    for _ in range(reps):
+        hst.copy_(dev, non_blocking=True)
+    c1.record()
+    torch.cuda.synchronize()
+    link = reps * nbytes / (c0.elapsed_time(c1) / 1e3) / 1e9
+    del dev, hst, v0
+    achieved = per_step * n_steps / (ms / 1e3) / 1e9
     return {"value": eng.n_envs * n_steps / (ms / 1e3), "unit": "env-steps/s",
             "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(per_step),
-            "note": "per env-step: every output ring slot (%s) copied to pinned host memory"
-                    % ", ".join(k for k, _ in ex)}
+            "d2h_gbs": achieved, "d2h_link_peak_gbs": link, "link_frac": achieved / link,
+            "note": "per env-step: every output ring slot (%s) copied to pinned host memory, overlapped with the "
+                    "next chunk's steps; link peak = the same chunk bytes copied alone" % ", ".join(k for k, _ in ex)}
 
 
 def _oracle_shard(job):
@@ -566,7 +669,7 @@ def run_served(args):
 
     hase.hase_serve(W.served_requests(duration=0.05), budget, n_streams=args.streams)  # warm-up
     reqs = W.served_requests(duration=args.duration)
-    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks = clock_sampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
     s, stats, res = serve(reqs, 1.0)  # the stream at its own pace: 2,000 requests/s
     clk = clocks.stop()
