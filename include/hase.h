@@ -98,10 +98,16 @@ typedef enum hase_status {
                                 /* 2 seen seekers, 3 seen hiders -- each S   */
                                 /* rows of one uint64 (bit x = column x)     */
 #define HASE_DESYNC_START 16u  /* desynchronised start [Sec. 3.3, last    */
-                                /* paragraph]: env e's episode clock starts  */
-                                /* at floor(u * cap / 2^32), u = word 0 of   */
-                                /* Philox counter (0, 0, env, 3), at create  */
-                                /* and at every hase_reset                   */
+                                /* paragraph: stepped stochastically at      */
+                                /* initialisation]: env e takes o_e =        */
+                                /* floor(u * cap / 2^32) moves from its      */
+                                /* start cells before its first observation, */
+                                /* u = word 0 of Philox counter (0, 0, env,  */
+                                /* 3); move tau draws word tau % 4 of        */
+                                /* counter (tau / 4, agent, env, 4); its     */
+                                /* episode clock starts at o_e (its first    */
+                                /* episode ends cap - o_e steps later), at   */
+                                /* create and at every hase_reset            */
 #define HASE_EXPORT_STATE 64u  /* also write the true state [Sec. 3.3,      */
                                 /* modes 2, 4, 5]: after every step the cell */
                                 /* of every agent and the episode clock of   */
@@ -222,7 +228,11 @@ typedef struct hase_digest_out {
                          /* splitmix64(obs[s][j] ^ (s * obs_words + j))     */
     uint64_t episodes;   /* done bits over the steps and envs                */
     int64_t reward_sum;  /* rewards over the steps and agents                */
-    uint32_t gen_error;  /* nonzero: the world generation failed             */
+    uint32_t gen_error;  /* the handle's error word, 0 = none: bit 0 the     */
+                         /* world generation failed, bit 1 a bounded wait of */
+                         /* the streaming step ran out, bit 2 a CTA's shared-*/
+                         /* memory plan exceeded its launch (bits 1-2: the   */
+                         /* outputs are incomplete)                          */
     uint32_t pad;
 } hase_digest_out;
 
@@ -236,8 +246,9 @@ typedef struct hase_digest_out {
  * memory runs out, HASE_ECUDA for other CUDA errors; *out is NULL then. */
 hase_status hase_create(const hase_config *cfg, void *stream, hase_handle **out);
 
-/* Back to t = 0: start cells, episode counters 0 (or the desynchronised
- * offsets), step -1 observation.  [Sec. 4.2: a reset restores the pristine
+/* Back to t = 0: start cells, episode counters 0 (with HASE_DESYNC_START:
+ * the offsets, and the moves taken before the first observation), step -1
+ * observation.  [Sec. 4.2: a reset restores the pristine
  * initial state.] */
 hase_status hase_reset(hase_handle *h, void *stream);
 
@@ -341,7 +352,10 @@ hase_status hase_get_world(hase_handle *h, uint32_t e, uint8_t *grid, int32_t *s
 
 /* Wait for all work the handle enqueued; HASE_ETIMEOUT when a bounded wait
  * of the streaming step kernel ran out (its outputs are then incomplete),
- * HASE_EINVAL when the world generation failed.  Not in the paper. */
+ * HASE_ECUDA when a CTA found its shared-memory plan larger than its launch
+ * and returned without stepping (an internal sizing error: the host sizes
+ * every launch by the same plan), HASE_EINVAL when the world generation
+ * failed.  Not in the paper. */
 hase_status hase_sync(hase_handle *h);
 
 /* Number of CTAs and dynamic shared memory of one step launch, and the

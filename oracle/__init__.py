@@ -57,6 +57,8 @@ def load_library(path):
     L.ho_philox4x32_10.argtypes = [P, P, P]
     L.ho_action.argtypes = [u64, u64, u32, u32]
     L.ho_action.restype = u32
+    L.ho_prestep_action.argtypes = [u64, u32, u32, u32]
+    L.ho_prestep_action.restype = u32
     L.ho_move.argtypes = [u32, P, u32, P, P, P, P, P]
     L.ho_reward.argtypes = [u32, u32, u32, P, P, P]
     L.ho_observe_agent.argtypes = [u32, P, u32, u32, P, P, u32, u32, u32, u32, P]
@@ -123,6 +125,10 @@ def philox4x32_10(ctr, key, L=None):
 
 def action(seed, t, agent, env_id, L=None):
     return int((L or lib()).ho_action(seed, t, agent, env_id))
+
+
+def prestep_action(seed, tau, agent, env_id, L=None):
+    return int((L or lib()).ho_prestep_action(seed, tau, agent, env_id))
 
 
 def splitmix64(z, L=None):

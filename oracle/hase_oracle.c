@@ -540,17 +540,46 @@ void ho_destroy(ho_world *w) {
 
 /* Desynchronised start (Section 3.3, last paragraph: the envs of a batch are
  * stepped stochastically at initialisation so that they do not all end their
- * episodes together).  Reading: only the episode clock is offset -- env e
- * starts its first episode at step floor(u * cap / 2^32), u = word 0 of the
- * Philox block of counter (0, 0, env id, 3) -- so its first episode is that
- * much shorter; positions start at the pristine cells and the action counter
- * is untouched. */
+ * episodes together).  Reading: env e draws an offset o_e = floor(u * cap /
+ * 2^32), u = word 0 of the Philox block of counter (0, 0, env id, 3), and
+ * takes o_e steps of its dynamics (a1 actions, a2/a3 moves) from its start
+ * cells before its first observation.  Those steps draw their actions from a
+ * stream of their own -- pre-step tau uses word tau % 4 of counter
+ * (tau / 4, agent, env id, 4) -- and give no reward, observation or fog
+ * update; the env's episode clock starts at o_e, so its first episode ends
+ * after cap - o_e more steps (o_e < cap: no episode ends while pre-stepping),
+ * and every later episode starts from the start cells.  The action stream of
+ * the steps themselves (stream 0, counter t) is untouched. */
 static uint32_t start_offset(const ho_world *w, uint32_t e) {
     const uint32_t ctr[4] = {0u, 0u, w->env_id_base + e, 3u};
     const uint32_t key[2] = {(uint32_t)(w->seed & 0xffffffffu), (uint32_t)(w->seed >> 32)};
     uint32_t out[4];
     ho_philox4x32_10(ctr, key, out);
     return mulhi32(out[0], w->env[e].cap);
+}
+
+/* Stream 4: the action of pre-step tau of the desynchronised start. */
+uint32_t ho_prestep_action(uint64_t seed, uint32_t tau, uint32_t agent, uint32_t env_id) {
+    uint32_t out[4];
+    philox_words(seed, tau >> 2, agent, env_id, 4u, out);
+    return mulhi32(out[tau & 3u], 5u);
+}
+
+/* n pre-steps of env e: actions of stream 4, then the simultaneous moves. */
+static void prestep_env(ho_world *w, uint32_t e, uint32_t n) {
+    const ho_env *p = &w->env[e];
+    const uint32_t A = p->n_agents, env_id = w->env_id_base + e;
+    const uint64_t base = w->agent_off[e];
+    uint8_t act[256];
+    int32_t nx[256], ny[256];
+    for (uint32_t tau = 0; tau < n; ++tau) {
+        for (uint32_t a = 0; a < A; ++a) act[a] = (uint8_t)ho_prestep_action(w->seed, tau, a, env_id);
+        ho_move(p->side, w->grid[e], A, &w->x[base], &w->y[base], act, nx, ny);
+        for (uint32_t a = 0; a < A; ++a) {
+            w->x[base + a] = nx[a];
+            w->y[base + a] = ny[a];
+        }
+    }
 }
 
 void ho_set_desync(ho_world *w, int on) {
@@ -567,6 +596,7 @@ void ho_reset(ho_world *w) {
             w->x[i] = w->sx[i];
             w->y[i] = w->sy[i];
         }
+        if (w->desync) prestep_env(w, e, w->ep_t[e]);
         if (w->fog) fog_env(w, e, 1u);
     }
 }

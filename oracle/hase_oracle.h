@@ -106,10 +106,16 @@ void ho_central_one(uint32_t side, const uint8_t *grid, uint32_t A, uint32_t n_s
                     uint32_t r_hide, uint32_t obs_teams, const int32_t *x, const int32_t *y, uint64_t *out);
 void ho_central(const ho_world *w, uint64_t *out);
 
-/* Desynchronised start on (1) or off (0), then ho_reset.  With it on, env e's
- * episode clock starts at floor(u * cap / 2^32), u = word 0 of the Philox
- * block of counter (0, 0, env id, 3) (Section 3.3, last paragraph). */
+/* Desynchronised start on (1) or off (0), then ho_reset.  With it on, env e
+ * takes o_e = floor(u * cap / 2^32) steps of its dynamics from the start
+ * cells before its first observation, u = word 0 of the Philox block of
+ * counter (0, 0, env id, 3), and its episode clock starts at o_e (Section
+ * 3.3, last paragraph). */
 void ho_set_desync(ho_world *w, int on);
+
+/* Action of pre-step tau (0 <= tau < o_e) of the desynchronised start: word
+ * tau % 4 of the Philox block of counter (tau / 4, agent, env id, 4). */
+uint32_t ho_prestep_action(uint64_t seed, uint32_t tau, uint32_t agent, uint32_t env_id);
 
 /* Per-step output sizes: agents (rewards/actions), packed obs words and
  * unpacked obs bytes of one step over all envs. */

@@ -18,6 +18,8 @@
 namespace hase {
 cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_envs, const uint2* keys,
                             uint16_t* pos, uint16_t* start, uint64_t* rows, uint32_t* err, cudaStream_t st);
+cudaError_t launch_prestep(const EnvRT* env, uint32_t n_envs, const uint2* keys, const EnvState* est,
+                           const uint64_t* rows, uint16_t* pos, cudaStream_t st);
 cudaError_t launch_observe(const EnvRT* env, uint32_t n_envs, const uint16_t* pos,
                            const uint64_t* rows, uint64_t* obs, uint8_t* unp, cudaStream_t st);
 cudaError_t launch_step(int family, bool stream, const StepParams& p, uint32_t n_groups, uint32_t threads,
@@ -555,6 +557,10 @@ hase_status hase_create(const hase_config* cfg, void* stream, hase_handle** out)
     if ((s = finish(launch_generate(h->d_env, h->d_thr, h->n_envs, h->d_keys, h->d_pos, h->d_start, h->d_rows,
                                     h->d_err, st), "generate")) != HASE_OK)
         return s;
+    if ((h->flags & HASE_DESYNC_START) &&
+        (s = finish(launch_prestep(h->d_env, h->n_envs, h->d_keys, h->d_est, h->d_rows, h->d_pos, st),
+                    "desynchronised start")) != HASE_OK)
+        return s;
     const uint64_t last = R - 1;
     if ((s = finish(launch_observe(h->d_env, h->n_envs, h->d_pos, h->d_rows, h->d_obs + last * h->obs_words,
                                    h->d_unp ? h->d_unp + last * h->unp_bytes : nullptr, st),
@@ -609,6 +615,8 @@ hase_status hase_reset(hase_handle* h, void* stream) {
     HASE_CUDA(h, cudaMemcpyAsync(h->d_pos, h->d_start, 2 * h->agents, cudaMemcpyDeviceToDevice, st));
     HASE_CUDA(h, cudaMemcpyAsync(h->d_est, h->est0.data(), sizeof(EnvState) * h->n_envs, cudaMemcpyHostToDevice,
                                  st));
+    if (h->flags & HASE_DESYNC_START)
+        HASE_CUDA(h, launch_prestep(h->d_env, h->n_envs, h->d_keys, h->d_est, h->d_rows, h->d_pos, st));
     HASE_CUDA(h, cudaMemsetAsync(h->d_rew + last * h->agents, 0, 4 * h->agents, st));
     HASE_CUDA(h, cudaMemsetAsync(h->d_done + last * h->n_envs, 0, h->n_envs, st));
     if (h->d_act) HASE_CUDA(h, cudaMemsetAsync(h->d_act + last * h->agents, 0, h->agents, st));
@@ -900,6 +908,8 @@ hase_status hase_sync(hase_handle* h) {
     HASE_CUDA(h, cudaMemcpy(&herr, h->d_err, 4, cudaMemcpyDeviceToHost));
     if (herr & kErrWaitTimeout)
         return fail(h, HASE_ETIMEOUT, "a bounded wait of the step kernel ran out; the outputs are incomplete");
+    if (herr & kErrSmemPlan)
+        return fail(h, HASE_ECUDA, "a CTA's shared-memory plan exceeded its launch; the outputs are incomplete");
     if (herr) return fail(h, HASE_EINVAL, "start-cell draw did not terminate");
     return HASE_OK;
 }

@@ -233,6 +233,17 @@ constexpr uint32_t kActRing = 16;      // Philox blocks (quads of steps) per age
 constexpr uint32_t kStreamGroup = 16;  // steps between the dynamics' progress updates
 constexpr uint32_t kStreamMinOutRing = 2 * kStreamRing + 32;  // output ring steps the streaming form needs
 constexpr uint32_t kErrWaitTimeout = 2u;  // error-word bit: a bounded wait of the step ran out
+constexpr uint32_t kErrSmemPlan = 4u;     // error-word bit: a CTA's shared-memory plan exceeds its launch's
+                                          // dynamic shared memory (the CTA returns before touching it)
+
+#ifdef __CUDACC__
+// Dynamic shared memory of the running launch, in bytes.
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+#endif
 
 // Shared-memory plan of one CTA of the streaming form (the dynamics state
 // bytes, obstacle rows and window tables as in plan_group; no claim words,

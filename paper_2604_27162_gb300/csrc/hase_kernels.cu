@@ -3,6 +3,8 @@
 //
 //   gen_kernel      a0: start cells and Bernoulli obstacle rows (Sec. 3.2,
 //                   Sec. 4.2 pristine template), one warp per env
+//   prestep_kernel  the desynchronised start: each env's moves before its
+//                   first observation (Sec. 3.3, last paragraph)
 //   observe_kernel  the step -1 observation after create / reset (and
 //                   central_init_kernel, state_init_kernel, fog_init_kernel:
 //                   its centralized observation, true state and fog of war)
@@ -89,6 +91,74 @@ __global__ void gen_kernel(const EnvRT* __restrict__ env, const uint32_t* __rest
         out[pr * rw] = w0;
         if (rw == 2) out[pr * rw + 1] = w1;
     }
+}
+
+// --------------------------------------------------------------------------
+// Desynchronised start (Sec. 3.3, last paragraph: the envs of a batch are
+// stepped stochastically at initialisation).  Env e takes ep_t(e) steps of
+// its dynamics from the start cells before its first observation, with
+// actions of their own Philox stream: pre-step tau uses word tau % 4 of
+// counter (tau / 4, agent, env id, 4).  A move is valid when the action is
+// not "stay" and the target is inside the grid, free of obstacles and not
+// any agent's current cell; among valid movers with the same target the
+// lowest agent index moves.  One warp per env, lane a = agent a; ep_t < cap,
+// so no episode ends, and nothing is written but the positions.
+// --------------------------------------------------------------------------
+__global__ void prestep_kernel(const EnvRT* __restrict__ env, uint32_t n_envs, const uint2* __restrict__ keys,
+                               const EnvState* __restrict__ est, const uint64_t* __restrict__ rows,
+                               uint16_t* __restrict__ pos) {
+    const uint32_t e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const uint32_t lane = threadIdx.x & 31;
+    if (e >= n_envs) return;  // whole warps
+    const EnvRT E = env[e];
+    const uint32_t A = E.n_agents, rw = E.rw;
+    const uint64_t* R = rows + E.rows_off;
+    const bool live = lane < A;
+    int x = 0, y = 0;
+    if (live) {
+        const uint32_t p = pos[E.agent_off + lane];
+        x = (int)px(p);
+        y = (int)py(p);
+    }
+    const uint32_t n = est[e].ep_t, key0 = keys[e].x, key1 = keys[e].y;
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t tau = 0; tau < n; ++tau) {
+        if ((tau & 3u) == 0u) {
+            uint32_t c0 = tau >> 2, c1 = lane, c2 = E.env_id, c3 = 4u;
+            philox4x32_10(c0, c1, c2, c3, key0, key1);
+            w[0] = c0;
+            w[1] = c1;
+            w[2] = c2;
+            w[3] = c3;
+        }
+        const uint32_t u = (tau & 3u) == 0u ? w[0] : (tau & 3u) == 1u ? w[1] : (tau & 3u) == 2u ? w[2] : w[3];
+        const uint32_t act = mulhi_n(u, 5u);  // 0 stay, 1 N, 2 S, 3 E, 4 W
+        const int tx = x + (act == 3u) - (act == 4u);
+        const int ty = y + (act == 2u) - (act == 1u);
+        bool ok = live && act != 0u;
+        if (ok) {  // padded rows: row ty + kPad, bit tx + kPad; outside the grid reads blocked
+            const uint32_t bit = (uint32_t)(tx + kPad);
+            ok = ((R[(uint32_t)(ty + kPad) * rw + (bit >> 6)] >> (bit & 63u)) & 1ull) == 0ull;
+        }
+        const uint32_t cur = live ? pack_xy((uint32_t)x, (uint32_t)y) : 0xffffffffu;
+        const uint32_t tgt = ok ? pack_xy((uint32_t)tx, (uint32_t)ty) : 0xfffffffeu;
+        // every lane takes part in every shuffle (no short-circuit around them)
+        for (uint32_t b = 0; b < A; ++b) {  // target held by some agent now
+            const uint32_t cb = __shfl_sync(0xffffffffu, cur, b);
+            ok = ok && cb != tgt;
+        }
+        const uint32_t claim = ok ? tgt : 0xfffffffeu;
+        bool moves = ok;
+        for (uint32_t b = 0; b < A; ++b) {  // a lower valid mover wants the same cell
+            const uint32_t cl = __shfl_sync(0xffffffffu, claim, b);
+            moves = moves && !(b < lane && cl == claim);
+        }
+        if (moves) {
+            x = tx;
+            y = ty;
+        }
+    }
+    if (live) pos[E.agent_off + lane] = (uint16_t)pack_xy((uint32_t)x, (uint32_t)y);
 }
 
 // --------------------------------------------------------------------------
@@ -219,6 +289,14 @@ cudaError_t launch_generate(const EnvRT* env, const uint32_t* thr, uint32_t n_en
     const uint32_t wpb = 4;
     gen_kernel<<<(n_envs + wpb - 1) / wpb, wpb * 32, 0, st>>>(env, thr, n_envs, keys, pos, start,
                                                               rows, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prestep(const EnvRT* env, uint32_t n_envs, const uint2* keys, const EnvState* est,
+                           const uint64_t* rows, uint16_t* pos, cudaStream_t st) {
+    if (n_envs == 0) return cudaSuccess;
+    const uint32_t wpb = 4;
+    prestep_kernel<<<(n_envs + wpb - 1) / wpb, wpb * 32, 0, st>>>(env, n_envs, keys, est, rows, pos);
     return cudaGetLastError();
 }
 

@@ -1102,6 +1102,10 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
         plan_group(H.env, ne, (int)kc, G.flags, H.plan);
     }
     __syncthreads();
+    if (H.plan.total > dynamic_smem_bytes()) {  // the host sized the launch by the same plan: cannot happen
+        if (tid == 0) atomicOr(P.err, kErrSmemPlan);
+        return;  // the whole CTA (H.plan is shared)
+    }
     const GroupPlan& L = H.plan;
     const bool use_table = L.flags & kUseTable;
     uint8_t* s_act = sm + L.act;                     // [3][act_words] (bytes of 4 steps)

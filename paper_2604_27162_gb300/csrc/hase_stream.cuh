@@ -624,6 +624,10 @@ __global__ void __launch_bounds__(MAXT, 1) stream_kernel(const StepParams P) {
     // an emission warp has read every step before its first block
     if (tid < kMaxEmitWarps) H.emit_prog[tid] = min(P.n_steps, (32u * (uint32_t)tid) / (uint32_t)ne);
     __syncthreads();
+    if (H.plan.total > dynamic_smem_bytes()) {  // the host sized the launch by the same plan: cannot happen
+        if (tid == 0) atomicOr(P.err, kErrSmemPlan);
+        return;  // the whole CTA (H.plan is shared)
+    }
     const GroupPlan& L = H.plan;
     const bool use_table = L.flags & kUseTable;
     uint64_t* s_rows = reinterpret_cast<uint64_t*>(sm + L.rows);

@@ -277,6 +277,20 @@ def _modes(L):
                 first[e] = t + 1
     if first != [cap - v for v in want]:
         return False
+    # ... and the env took that many moves from its start cells, actions from
+    # Philox counter (tau / 4, agent, env, 4), word tau % 4
+    A, S = 3, 8
+    w = oracle.World(n, seed, [W.env_desc(S, A, 1, 1, 1, cap, "0.1")], L=L, desync=True)
+    st = w.state()
+    for e in range(n):
+        sl = slice(A * e, A * e + A)
+        x, y = st["sx"][sl].astype(np.int32), st["sy"][sl].astype(np.int32)
+        g = w.grid(e).reshape(S, S)
+        for tau in range(int(st["ep_t"][e])):
+            act = [(int(oracle.philox4x32_10((tau // 4, a, e, 4), key, L=L)[tau % 4]) * 5) >> 32 for a in range(A)]
+            x, y = oracle.move(S, g, x, y, np.array(act, np.uint8), L=L)
+        if not (np.array_equal(x, st["x"][sl]) and np.array_equal(y, st["y"][sl])):
+            return False
     # true state: the hand case, and the full-view centralized planes
     c = cases["true_state"]
     x, y = _xy(c["agents"])

@@ -115,6 +115,18 @@ def test_desynchronised_start_matches_oracle():
     eng.close()
 
 
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_desynchronised_start_moves_match_oracle(form):
+    """The moves taken before the first observation (Sec. 3.3, last
+    paragraph): the step -1 cells and clocks, then every step, with an
+    env-id offset, in both step forms (the streaming form serves up to 16
+    agents; 20 and 32 run chunked)."""
+    flags = hase.HASE_EXPORT_STATE | hase.HASE_EXPORT_ACTIONS | hase.HASE_DESYNC_START | FORMS[form]
+    for A, S, cap in ((2, 16, 40), (10, 32, 60), (20, 16, 50), (32, 24, 90)):
+        descs = [W.env_desc(S, A, max(1, A // 2), 3, 2, cap, "0.2")]
+        compare_run(24, 31, descs, 70, ring=200, flags=flags, env_id_base=1000, launches=[33, 37])
+
+
 @pytest.mark.parametrize("desc", [
     W.env_desc(32, 10, 5, 3, 2, 40, "0.2", 3 | 4),     # one-thread emission, radius 3 / 2
     W.env_desc(24, 7, 4, 4, 4, 40, "0.25", 3 | 4),     # one-thread emission, radius 4 (two words)

@@ -57,6 +57,11 @@ MUTANTS = [
     ("central ignores observing teams", "                if (!((obs_teams >> team) & 1u)) continue;\n                const int32_t r = (int32_t)(team ? r_hide : r_seek);",
      "                const int32_t r = (int32_t)(team ? r_hide : r_seek);"),
     ("desync offset word", "return mulhi32(out[0], w->env[e].cap);", "return mulhi32(out[1], w->env[e].cap);"),
+    ("pre-steps from the step stream", "philox_words(seed, tau >> 2, agent, env_id, 4u, out);",
+     "philox_words(seed, tau >> 2, agent, env_id, 0u, out);"),
+    ("one pre-step fewer", "for (uint32_t tau = 0; tau < n; ++tau) {", "for (uint32_t tau = 1; tau < n; ++tau) {"),
+    ("pre-step word", "return mulhi32(out[tau & 3u], 5u);", "return mulhi32(out[(tau + 1u) & 3u], 5u);"),
+    ("no pre-steps", "if (w->desync) prestep_env(w, e, w->ep_t[e]);", "if (w->desync) prestep_env(w, e, 0u);"),
     ("fog map kept across episodes", "const uint8_t before = start ? 0 : d[c];", "const uint8_t before = d[c];"),
     ("fog fresh is the whole map", "f[c] = (uint8_t)(seen && !before);", "f[c] = (uint8_t)(before | seen);"),
     ("fog per-agent unit ignores its agent", "const uint32_t mine = !per_agent || k == u;",

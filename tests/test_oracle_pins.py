@@ -485,31 +485,78 @@ def test_invalid_params_rejected():
 def test_desynchronised_start():
     """Section 3.3 (last paragraph): with the desynchronised start the first
     episode of env e lasts cap - offset(e) steps, offsets spread uniformly over
-    [0, cap), positions start at the pristine cells, and every later episode
-    lasts cap steps."""
+    [0, cap), and every later episode lasts cap steps from the start cells."""
     cap = 16
     n = 4000
     descs = [W.env_desc(8, 3, 2, 1, 1, cap, "0.1")]
     plain = oracle.World(n, 21, descs)
     w = oracle.World(n, 21, descs, desync=True)
     s0, s1 = plain.state(), w.state()
-    x0, y0, ep0 = s0["x"], s0["y"], s0["ep_t"].astype(np.int64)
-    x1, y1, ep1 = s1["x"], s1["y"], s1["ep_t"].astype(np.int64)
-    assert np.array_equal(x0, x1) and np.array_equal(y0, y1)
+    ep0, ep1 = s0["ep_t"].astype(np.int64), s1["ep_t"].astype(np.int64)
+    assert np.array_equal(s0["sx"], s1["sx"]) and np.array_equal(s0["sy"], s1["sy"])  # same start cells
     assert (ep0 == 0).all() and ep1.min() >= 0 and ep1.max() < cap
     counts = np.bincount(ep1, minlength=cap)
     expected = n / cap
     chi2 = float(((counts - expected) ** 2 / expected).sum())
     assert chi2 < 40.0, chi2  # 15 degrees of freedom, p ~ 5e-4
-    first = np.full(n, -1)
     ends = [[] for _ in range(n)]
     for t in range(3 * cap):
         d = w.step()["done"]
         for e in np.flatnonzero(d):
             ends[e].append(t)
+            if len(ends[e]) == 1:  # the first reset puts the env back on its start cells
+                st = w.state()
+                sl = slice(3 * e, 3 * e + 3)
+                assert np.array_equal(st["x"][sl], st["sx"][sl]) and np.array_equal(st["y"][sl], st["sy"][sl])
     for e in range(n):
         assert ends[e][0] == cap - 1 - ep1[e], e
         assert all(b - a == cap for a, b in zip(ends[e], ends[e][1:])), e
+
+
+def _prestep_replay(seed, S, grid, sx, sy, n, env_id):
+    """n pre-steps from (sx, sy) rebuilt from the pinned parts: Philox blocks
+    of counter (tau / 4, agent, env, 4), word tau % 4 scaled to 0..4, and the
+    simultaneous move rule."""
+    x, y = np.array(sx, np.int32), np.array(sy, np.int32)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for tau in range(n):
+        act = [(int(oracle.philox4x32_10((tau // 4, a, env_id, 4), key)[tau % 4]) * 5) >> 32 for a in range(len(x))]
+        x, y = oracle.move(S, grid, x, y, np.array(act, np.uint8))
+    return x, y
+
+
+def test_desynchronised_start_steps_the_dynamics():
+    """Section 3.3 (last paragraph): the envs are stepped stochastically at
+    initialisation -- env e takes offset(e) moves from its start cells, with
+    actions of their own Philox stream, before its first observation.  The
+    positions equal a replay of those moves, stay legal (inside the grid, off
+    obstacles, one agent per cell, within offset(e) cells of the start), an
+    env with offset 0 stays on its start cells, and longer offsets carry the
+    agents further on average."""
+    cap, n, seed = 40, 300, 5
+    A = 4
+    descs = [W.env_desc(10, A, 2, 1, 1, cap, "0.15")]
+    w = oracle.World(n, seed, descs, env_id_base=7, desync=True)
+    st = w.state()
+    x, y, sx, sy, off = st["x"], st["y"], st["sx"], st["sy"], st["ep_t"].astype(np.int64)
+    dist = np.abs(x - sx) + np.abs(y - sy)
+    moved = []
+    for e in range(n):
+        sl = slice(A * e, A * e + A)
+        g = w.grid(e).reshape(10, 10)
+        rx, ry = _prestep_replay(seed, 10, g, sx[sl], sy[sl], int(off[e]), 7 + e)
+        assert np.array_equal(rx, x[sl]) and np.array_equal(ry, y[sl]), e
+        assert ((x[sl] >= 0) & (x[sl] < 10) & (y[sl] >= 0) & (y[sl] < 10)).all()
+        assert (g[y[sl], x[sl]] == 0).all()
+        assert len(set(zip(x[sl].tolist(), y[sl].tolist()))) == A
+        assert (dist[sl] <= off[e]).all()
+        if off[e] == 0:
+            assert (dist[sl] == 0).all()
+        moved.append(dist[sl].mean())
+    moved = np.array(moved)
+    assert (off == 0).any() and moved[off >= 20].mean() > moved[off < 5].mean() + 1.0
+    # the pre-step stream is not the step stream: counter word 3 is 4, not 0
+    assert any(oracle.prestep_action(seed, t, 0, 7) != oracle.action(seed, t, 0, 7) for t in range(8))
 
 
 def test_fog_of_war_equals_union_of_centralized_views():
