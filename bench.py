@@ -323,7 +323,10 @@ def build_form(form, c, run, flags, stream, base, log):
         t = time.perf_counter()
         knobs = [(k, v) for k, v in autotune.KNOBS if k != "step_form" or not flags & (
             H.HASE_CHUNKED_STEP | H.HASE_STREAM_STEP)]  # a form given on the command line is kept
-        setting, trials = autotune.tune(n_envs, c["seed"], c["descs"], flags, stream=stream, log=log, knobs=knobs)
+        # every candidate is timed on the run's own length: a shorter probe
+        # overweights the per-launch prologue of CTAs that run in waves
+        setting, trials = autotune.tune(n_envs, c["seed"], c["descs"], flags, probe_steps=run, stream=stream, log=log,
+                                        knobs=knobs)
         extra["autotune"] = {"setting": setting, "trials": len(trials),
                              "seconds": round(time.perf_counter() - t, 1)}
     eng = hase.Engine(n_envs, c["seed"], c["descs"], ring_steps=run, flags=flags, env_id_base=base,

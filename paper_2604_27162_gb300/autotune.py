@@ -4,9 +4,11 @@ The knobs are the ones `hase_create` takes: the form of the step kernel
 (chunked or streaming), the shared-memory cap of a CTA (which decides how
 many envs share a CTA and whether the per-cell window tables fit, hence how
 many CTAs an SM holds), the emission warps per CTA, the envs packed per CTA,
-the steps per on-chip chunk and the steps fused per launch.  Each candidate is measured on a short rollout of the actual batch,
-replayed as a CUDA graph exactly as the timed run will be, and the fastest
-is kept.  The search is coordinate descent from the engine's own defaults:
+the steps per on-chip chunk and the steps fused per launch.  Each candidate
+is measured on a rollout of the actual batch (by default 128 steps; give the
+timed run's own length where the per-launch prologue matters, e.g. CTAs that
+run in waves), replayed as a CUDA graph exactly as the timed run will be, and
+the fastest is kept.  The search is coordinate descent from the engine's own defaults:
 one knob at a time, keeping the best value before moving to the next.
 """
 from __future__ import annotations
