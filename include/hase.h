@@ -143,9 +143,8 @@ typedef enum hase_status {
                                 /* line of sight, no HASE_EXPORT_CENTRAL or  */
                                 /* HASE_EXPORT_FOG, ring_steps >= 160; by    */
                                 /* default it runs when the batch needs more */
-                                /* CTAs than the GPU has SMs or exports the  */
-                                /* unpacked observation.  These flags force  */
-                                /* one form (not both)                       */
+                                /* CTAs than the GPU has SMs.  These flags   */
+                                /* force one form (not both)                 */
 #define HASE_POOL_ALLOC 8u      /* buffers from the device's stream-ordered  */
                                 /* pool (allocated on the create stream,     */
                                 /* returned by hase_destroy on the stream of */

@@ -201,10 +201,10 @@ static bool streams(const hase_handle* h, int fam) {
     const bool can = fam >= 1 && fam <= 8 && !(h->base_flags & (kFog | kCentral)) && h->ring >= kStreamMinOutRing;
     if (!can || (h->flags & HASE_CHUNKED_STEP)) return false;
     // measured: the streaming form wins when CTAs run in waves (65,536 uneven
-    // envs: +13 %) and with the unpacked export, which it writes per step as
-    // contiguous runs (1024 envs x 2 agents: +38 %); it loses with one CTA
-    // per SM and packed planes only (1024 envs x 10 agents: -4 %)
-    return (h->flags & HASE_STREAM_STEP) || h->waves || h->unp_bytes > 0;
+    // envs: +13 %); with one CTA per SM the chunked form wins (1024 envs x 10
+    // agents: +8 %; 1024 envs x 2 agents with the unpacked export, both forms
+    // staging it: 8.1e9 against 6.3e9 env-steps/s)
+    return (h->flags & HASE_STREAM_STEP) || h->waves;
 }
 
 static bool plan_for(const hase_handle* h, const EnvRT* envs, int n, uint16_t flags, GroupPlan& plan) {
@@ -271,11 +271,11 @@ static bool make_groups(hase_handle* h, uint32_t max_envs_cfg, uint32_t n_sm) {
             plan_group(genv.data(), g.n_envs, (int)h->kc, flags | kUseTable | kSharedTable, plan);
             if (plan.total <= h->smem_budget) flags |= kUseTable | kSharedTable;
         }
-        if (streams(h, fam0) && h->unp_bytes) {  // stage the unpacked export when the envs are consecutive
+        if (fam0 >= 1 && h->unp_bytes) {  // the one-thread emission stages the unpacked export of consecutive envs
             bool consecutive = true;
             for (uint32_t j = 1; j < g.n_envs; ++j)
                 consecutive &= h->env_list[g.list_first + j] == h->env_list[g.list_first] + j;
-            if (consecutive && plan_stream(genv.data(), g.n_envs, flags | kUnpStage, plan) &&
+            if (consecutive && plan_for(h, genv.data(), g.n_envs, flags | kUnpStage, plan) &&
                 plan.total <= h->smem_budget)
                 flags |= kUnpStage;
         }

@@ -64,8 +64,9 @@ constexpr uint16_t kFogAgent = 4;   // with kFog: one unit per observing agent
 constexpr uint16_t kSharedTable = 8;  // with kUseTable: one table of the larger emitting radius
                                       // serves both teams (line-of-sight families)
 constexpr uint16_t kCentral = 16;     // centralized observation: two row buffers per emission warp
-constexpr uint16_t kUnpStage = 32;    // streaming form: the unpacked export is staged in shared memory and
-                                      // written per step as one contiguous run (envs consecutive in the layout)
+constexpr uint16_t kUnpStage = 32;    // the unpacked export is staged in shared memory by each emission warp
+                                      // and written per step as one contiguous run (envs consecutive in the
+                                      // layout; the one-thread emission of either form)
 
 // All envs of a group share the radii, the emitting teams, the row width and
 // the agent and seeker counts, so one code path serves the whole CTA.
@@ -156,6 +157,23 @@ __host__ __device__ inline uint32_t fog_units(const EnvRT& E, bool per_agent) {
     return (team_sees(E, 0) ? E.n_seekers : 0u) + (team_sees(E, 1) ? E.n_agents - E.n_seekers : 0u);
 }
 
+// Unpacked bytes of one env: 3 (2r + 1)^2 per emitting agent.
+__host__ __device__ inline uint32_t unpacked_bytes(const EnvRT& E) {
+    uint32_t unp = 0;
+    for (int a = 0; a < E.n_agents; ++a) {
+        const int t = a < E.n_seekers ? 0 : 1;
+        if (team_emits(E, t)) unp += 3u * (2u * team_radius(E, t) + 1u) * (2u * team_radius(E, t) + 1u);
+    }
+    return unp;
+}
+
+// Staging bytes of one emission warp for the unpacked export (kUnpStage): 32
+// (step, env) items, and up to 15 bytes before each step run of a block (at
+// most 32 runs), so that every run sits at its destination's offset mod 16.
+__host__ __device__ inline uint32_t stage_bytes_of(uint32_t unp_env) {
+    return align_up(32u * unp_env + 15u * 34u, 16);
+}
+
 // envs: the group's env constants in slot order.  Returns false when the
 // group does not fit the dynamics warps.
 __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uint16_t flags,
@@ -211,11 +229,13 @@ __host__ __device__ inline bool plan_group(const EnvRT* envs, int n, int kc, uin
     G.fog = align_up(G.state + co, 16);                  // uint64 per fog row
     G.cen = align_up(G.fog + fo * 8, 16);                // uint64 [emit warps][2][4][side]
     const uint32_t cen_words = (flags & kCentral) ? kMaxEmitWarps * 8u * max_side : 0u;
-    G.total = align_up(G.cen + cen_words * 8, 16);
+    G.stage = align_up(G.cen + cen_words * 8, 16);  // uint8 [kMaxEmitWarps][stage_bytes]
+    G.unp_env = n > 0 ? unpacked_bytes(envs[0]) : 0u;
+    G.stage_bytes = (flags & kUnpStage) ? stage_bytes_of(G.unp_env) : 0u;
+    G.total = align_up(G.stage + kMaxEmitWarps * G.stage_bytes, 16);
     G.prist = 0;
     G.rec_words = 0;
     G.ring = 0;
-    G.stage = G.stage_bytes = G.unp_env = 0;
     G.flags = flags;
     return true;
 }
@@ -299,18 +319,9 @@ __host__ __device__ inline bool plan_stream(const EnvRT* envs, int n, uint16_t f
     G.act_words = slot;                                           // uint32 action words of one quad
     G.act = align_up(G.claim + co * 4, 16);                       // uint32 [kActRing][slots]
     G.fog = G.cen = 0;
-    // unpacked bytes of one env: 3 (2r + 1)^2 per emitting agent
-    uint32_t unp = 0;
-    if (n > 0) {
-        const EnvRT& E = envs[0];
-        for (int a = 0; a < E.n_agents; ++a) {
-            const int t = a < E.n_seekers ? 0 : 1;
-            if (team_emits(E, t)) unp += 3u * (2u * team_radius(E, t) + 1u) * (2u * team_radius(E, t) + 1u);
-        }
-    }
-    G.unp_env = unp;
+    G.unp_env = n > 0 ? unpacked_bytes(envs[0]) : 0u;
     G.stage = align_up(G.act + kActRing * slot * 4, 16);          // uint8 [kMaxEmitWarps][stage_bytes]
-    G.stage_bytes = (flags & kUnpStage) ? align_up(32u * unp, 16) : 0u;
+    G.stage_bytes = (flags & kUnpStage) ? stage_bytes_of(G.unp_env) : 0u;
     G.total = align_up(G.stage + kMaxEmitWarps * G.stage_bytes, 16);
     G.flags = flags;
     return true;

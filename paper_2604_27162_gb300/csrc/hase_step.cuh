@@ -431,6 +431,7 @@ struct EmitCtx {
     uint32_t base_slot;     // ring slot of the chunk's first step
     uint32_t k0;            // steps of the launch before the chunk
     int worker, n_workers;  // this thread among the emission threads
+    uint8_t* stage;         // this warp's staging area of the unpacked export (kUnpStage)
 };
 
 // ---------------------------------------------------------------------------
@@ -682,37 +683,55 @@ struct TeamCtx {
     bool v16;             // the env's obs words start 16-byte aligned
 };
 
-// The unpacked export of one agent: bytes 0/1 of the three planes of DD
-// (<= 64) bits each, plane after plane.  Four bits at a time become one
-// 32-bit store: (b * 0x00204081) & 0x01010101 moves bit j of a 4-bit value b
-// to bit 0 of byte j.  Bytes before the first 4-byte boundary and after the
-// last one are stored singly.
+// Streaming (evict-first) global stores of the outputs.
+__device__ __forceinline__ void st_cs_u8(uint8_t* p, uint32_t a) { asm volatile("st.global.cs.u8 [%0], %1;" ::"l"(p), "r"(a)); }
+__device__ __forceinline__ void st_cs_v4(uint8_t* p, uint4 v) {
+    asm volatile("st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w));
+}
+
+// The unpacked export of one agent: byte i of its 3 DD bytes (DD <= 64) is
+// bit i of the string p0 | p1 << DD | p2 << 2 DD (plane after plane; bits of
+// a plane above DD are 0).  The string is shifted by the h bytes before the
+// first 4-byte boundary of u, and every aligned 32-bit word then takes four
+// bits: (b * 0x00204081) & 0x01010101 moves bit j of a 4-bit value b to bit
+// 0 of byte j.  The h bytes and the bytes after the last boundary are stored
+// singly.
 __device__ __forceinline__ void unpack_planes(uint8_t* u, uint64_t p0, uint64_t p1, uint64_t p2, uint32_t DD) {
     const uint32_t n = 3u * DD;
-    uint32_t i = 0, p = 0, off = 0;  // byte i is bit `off` of plane p
-    auto plane = [&](uint32_t q) { return q == 0 ? p0 : (q == 1 ? p1 : p2); };
-    auto advance = [&](uint32_t k) {
-        off += k;
-        while (off >= DD) {
-            off -= DD;
-            ++p;
-        }
+    uint64_t s0 = p0, s1 = 0ull, s2 = 0ull;  // the string, bits 0-63, 64-127, 128-191
+    auto put = [&](uint64_t v, uint32_t b) {  // OR v in at bit b (b + 64 <= 192 or v short enough)
+        const uint32_t q = b >> 6, r = b & 63u;
+        const uint64_t lo = v << r, hi = r ? v >> (64u - r) : 0ull;
+        s0 |= q == 0u ? lo : 0ull;
+        s1 |= q == 1u ? lo : (q == 0u ? hi : 0ull);
+        s2 |= q == 2u ? lo : (q == 1u ? hi : 0ull);
     };
-    while (i < n && (reinterpret_cast<uintptr_t>(u + i) & 3u)) {
-        u[i] = (uint8_t)((plane(p) >> off) & 1u);
-        ++i;
-        advance(1);
+    put(p1, DD);
+    put(p2, 2u * DD);
+    auto bit = [&](uint32_t b) -> uint32_t {
+        const uint64_t w = b < 64u ? s0 : (b < 128u ? s1 : s2);
+        return (uint32_t)(w >> (b & 63u)) & 1u;
+    };
+    const uint32_t h = min(n, (4u - ((uint32_t)reinterpret_cast<uintptr_t>(u) & 3u)) & 3u);
+    for (uint32_t i = 0; i < h; ++i) u[i] = (uint8_t)bit(i);
+    uint64_t t0 = s0, t1 = s1, t2 = s2;  // the string from bit h on
+    if (h) {
+        t0 = (s0 >> h) | (s1 << (64u - h));
+        t1 = (s1 >> h) | (s2 << (64u - h));
+        t2 = s2 >> h;
     }
-    for (; i + 4 <= n; i += 4) {
-        uint32_t b = (uint32_t)(plane(p) >> off);
-        if (off + 4 > DD) b = (b & ((1u << (DD - off)) - 1u)) | ((uint32_t)plane(p + 1) << (DD - off));
-        *reinterpret_cast<uint32_t*>(u + i) = ((b & 15u) * 0x00204081u) & 0x01010101u;
-        advance(4);
+    const uint32_t nq = (n - h) >> 2;  // whole words
+    uint32_t* w = reinterpret_cast<uint32_t*>(u + h);
+#pragma unroll 1
+    for (uint32_t g = 0; 16u * g < nq; ++g) {
+        const uint64_t t = g == 0u ? t0 : (g == 1u ? t1 : t2);
+#pragma unroll
+        for (uint32_t j = 0; j < 16u; ++j) {
+            const uint32_t q = 16u * g + j;
+            if (q < nq) w[q] = (((uint32_t)(t >> (4u * j)) & 15u) * 0x00204081u) & 0x01010101u;
+        }
     }
-    for (; i < n; ++i) {
-        u[i] = (uint8_t)((plane(p) >> off) & 1u);
-        advance(1);
-    }
+    for (uint32_t i = h + 4u * nq; i < n; ++i) u[i] = (uint8_t)bit(i);
 }
 
 // Observer a's three planes (obstacle, ally, opponent): bits 0-63 and, with
@@ -923,7 +942,7 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
 
 template <int A, bool W2, bool LOS>
 __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const CtaShared& H, const EmitCtx& C,
-                                                  uint32_t k, uint32_t e) {
+                                                  uint32_t k, uint32_t e, uint8_t* stage_item) {
     constexpr int NS = (A + 1) / 2, NW = (A + 3) / 4;
     const GroupPlan& L = H.plan;
     const EnvRT E = H.env[e];  // a register copy: the stores below cannot alias it
@@ -963,7 +982,9 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
         T.src = src;
         T.rows = C.rows + L.rows_off[e];
         T.ob = P.obs + (uint64_t)sl * P.obs_words + E.obs_off;
-        T.unp = P.unp ? P.unp + (uint64_t)sl * P.unp_bytes : nullptr;
+        // the unpacked planes of agent a go to unp + unp_rel(a): the slot in
+        // global memory, or this item's place in the warp's staging area
+        T.unp = !P.unp ? nullptr : (stage_item ? stage_item - E.unp_off : P.unp + (uint64_t)sl * P.unp_bytes);
         T.slot = H.slot + first;
         T.sh = sh;
         T.xmask = xmask;
@@ -1027,12 +1048,66 @@ __device__ __forceinline__ void emit_segment_fast(const StepParams& P, const Cta
 
 template <int A, bool W2, bool LOS>
 __device__ __forceinline__ void emit_segments_fast(const StepParams& P, const CtaShared& H, const EmitCtx& C) {
-    const uint32_t ne = H.plan.n_envs;
+    const GroupPlan& L = H.plan;
+    const uint32_t ne = L.n_envs;
     const uint32_t total = C.len * ne;
     const uint32_t dk = (uint32_t)C.n_workers / ne, de = (uint32_t)C.n_workers % ne;
     uint32_t k = (uint32_t)C.worker / ne, e = (uint32_t)C.worker % ne;
-    for (uint32_t it = (uint32_t)C.worker; it < total; it += (uint32_t)C.n_workers) {
-        emit_segment_fast<A, W2, LOS>(P, H, C, k, e);
+    if (!((L.flags & kUnpStage) && P.unp)) {
+        for (uint32_t it = (uint32_t)C.worker; it < total; it += (uint32_t)C.n_workers) {
+            emit_segment_fast<A, W2, LOS>(P, H, C, k, e, nullptr);
+            e += de;
+            k += dk;
+            if (e >= ne) {
+                e -= ne;
+                ++k;
+            }
+        }
+        return;
+    }
+    // The unpacked export staged per warp: a round's 32 consecutive items
+    // form one contiguous run per step (envs e_a..e_b of step kk sit at
+    // unp_off[e_a] of its slot); each run is staged at an offset congruent
+    // to its destination mod 16 and leaves with 16-byte stores.
+    const int lane = C.worker & 31;
+    uint8_t* const stage = C.stage;
+    auto run_dst = [&](uint32_t kk, uint32_t e_a) {
+        uint32_t sl = C.base_slot + kk;
+        if (sl >= P.ring) sl -= P.ring;
+        return P.unp + (uint64_t)sl * P.unp_bytes + H.env[e_a].unp_off;
+    };
+    for (uint32_t i0 = (uint32_t)C.worker - (uint32_t)lane; i0 < total; i0 += (uint32_t)C.n_workers) {
+        const uint32_t i = i0 + (uint32_t)lane, last = min(i0 + 31u, total - 1u);
+        const uint32_t k_a = i0 / ne, k_b = last / ne;
+        if (i < total) {
+            uint32_t off = 0;
+            uint8_t* stage_item = nullptr;
+            for (uint32_t kk = k_a; kk <= k; ++kk) {
+                const uint32_t first = max(i0, kk * ne), end = min(last + 1u, (kk + 1u) * ne);
+                off += ((uint32_t)reinterpret_cast<uintptr_t>(run_dst(kk, first - kk * ne)) - off) & 15u;
+                if (kk == k) stage_item = stage + off + (i - first) * L.unp_env;
+                off += (end - first) * L.unp_env;
+            }
+            emit_segment_fast<A, W2, LOS>(P, H, C, k, e, stage_item);
+        }
+        __syncwarp();  // every lane has staged its bytes
+        uint32_t off = 0;
+        for (uint32_t kk = k_a; kk <= k_b; ++kk) {
+            const uint32_t first = max(i0, kk * ne), end = min(last + 1u, (kk + 1u) * ne);
+            uint8_t* g = run_dst(kk, first - kk * ne);
+            const uint32_t mis = (uint32_t)reinterpret_cast<uintptr_t>(g) & 15u;
+            off += (mis - off) & 15u;
+            const uint8_t* src = stage + off;  // src = g mod 16
+            const uint32_t len = (end - first) * L.unp_env;
+            const uint32_t head = min(len, (16u - mis) & 15u);
+            const uint32_t body = (len - head) >> 4, tail0 = head + 16u * body;
+            if ((uint32_t)lane < head) st_cs_u8(g + lane, src[lane]);
+            for (uint32_t c = (uint32_t)lane; c < body; c += 32u)
+                st_cs_v4(g + head + 16u * c, *reinterpret_cast<const uint4*>(src + head + 16u * c));
+            if ((uint32_t)lane < len - tail0) st_cs_u8(g + tail0 + lane, src[tail0 + lane]);
+            off += len;
+        }
+        __syncwarp();  // the staging area is read before the next round writes it
         e += de;
         k += dk;
         if (e >= ne) {
@@ -1378,6 +1453,7 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             C.k0 = cp * kc;
             C.worker = worker;
             C.n_workers = n_workers;
+            C.stage = sm + L.stage + (uint32_t)(warp - n_dyn) * L.stage_bytes;
             if constexpr (FAM > 0) {
                 emit_fast_dispatch<FAM>(H.env[0].n_agents, P, H, C);
             } else {

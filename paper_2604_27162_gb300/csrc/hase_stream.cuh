@@ -29,13 +29,13 @@
 //
 // With the unpacked export and envs consecutive in its layout, each emission
 // warp stages its block's unpacked bytes in shared memory and writes them per
-// step as one contiguous run (one 32-byte sector per warp store instead of a
-// sector per 4-byte store).
+// step as one contiguous run of 16-byte stores (the chunked form does the
+// same per round of its emission warps).
 //
 // Measured on a GB300 against the chunked form (step_kernel): +13 % on
-// 65,536 uneven envs (CTAs in waves), +38 % on 1024 envs x 2 agents with the
-// unpacked export, -4 % on 1024 envs x 10 agents (one CTA per SM, where the
-// dynamics chain of ~300 cycles a step under load bounds both).  A warp-wide __match_any_sync over the targets was tried for the
+// 65,536 uneven envs (CTAs in waves); -8 % on 1024 envs x 10 agents and -22 %
+// on 1024 envs x 2 agents with the unpacked export (one CTA per SM, where the
+// chunked dynamics step faster).  A warp-wide __match_any_sync over the targets was tried for the
 // collision round and measured at ~800 cycles with ~30 distinct keys (~45
 // with a handful): its cost grows with the number of distinct keys.
 //
@@ -305,6 +305,7 @@ __device__ __forceinline__ void gst_u8(uint8_t* p, uint32_t a) { asm volatile("s
 __device__ __forceinline__ void gst_u16(uint16_t* p, uint32_t a) { asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(p), "r"(a)); }
 __device__ __forceinline__ void gst_u32(uint32_t* p, uint32_t a) { asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(a)); }
 
+
 // Stores of one observer's words (three, or six with W2) at o, whose
 // 16-byte alignment is known from the address.
 template <bool W2>
@@ -524,22 +525,46 @@ __device__ __forceinline__ void stream_emit(const StepParams& P, StreamShared& H
             if (lane == 0) atomicOr(P.err, kErrWaitTimeout);
             return;
         }
-        if (i < n_items) stream_item<A, W2>(P, H, U, k, e, sl, stage ? stage + lane * L.unp_env : nullptr);
-        __syncwarp();  // every lane has read its record before the slots are handed back
+        // The block's unpacked bytes form one contiguous run per step (envs
+        // e_a..e_b of step kk sit at unp_off[e_a] of its slot).  Each run is
+        // staged at an offset congruent to its destination mod 16, so that it
+        // leaves with 16-byte stores; its items follow one another.
+        const uint32_t i0 = 32u * m, last = min(i0 + 31u, n_items - 1u);
+        const uint32_t k_a = i0 / ne, k_b = last / ne;
+        const uint32_t sl_a = __shfl_sync(0xffffffffu, sl, 0);  // slot of step k_a (lane 0 holds item i0)
+        auto run_dst = [&](uint32_t kk, uint32_t e_a) {
+            uint32_t sl_k = sl_a + (kk - k_a);  // kk - k_a <= 32 < ring: one wrap at most
+            if (sl_k >= ring) sl_k -= ring;
+            return P.unp + (uint64_t)sl_k * P.unp_bytes + H.env[e_a].unp_off;
+        };
+        uint8_t* stage_item = nullptr;
+        if (stage && i < n_items) {
+            uint32_t off = 0;
+            for (uint32_t kk = k_a; kk <= k; ++kk) {
+                const uint32_t first = max(i0, kk * ne), end = min(last + 1u, (kk + 1u) * ne);
+                off += ((uint32_t)reinterpret_cast<uintptr_t>(run_dst(kk, first - kk * ne)) - off) & 15u;
+                if (kk == k) stage_item = stage + off + (i - first) * L.unp_env;
+                off += (end - first) * L.unp_env;
+            }
+        }
+        if (i < n_items) stream_item<A, W2>(P, H, U, k, e, sl, stage_item);
+        __syncwarp();  // every lane has read its record (and staged its bytes)
         if (stage) {
-            // the block's unpacked bytes, one contiguous run per step: envs
-            // e_a..e_b of step kk sit at unp_off[e_a] of its slot, and at
-            // (item - first item) * unp_env in the staging area
-            const uint32_t i0 = 32u * m, last = min(i0 + 31u, n_items - 1u);
-            const uint32_t k_a = i0 / ne, k_b = last / ne;
+            uint32_t off = 0;
             for (uint32_t kk = k_a; kk <= k_b; ++kk) {
                 const uint32_t first = max(i0, kk * ne), end = min(last + 1u, (kk + 1u) * ne);
-                const uint32_t e_a = first - kk * ne;
-                const uint32_t sl_k = __shfl_sync(0xffffffffu, sl, (int)(first - i0));
-                uint8_t* g = P.unp + (uint64_t)sl_k * P.unp_bytes + H.env[e_a].unp_off;
-                const uint8_t* src = stage + (first - i0) * L.unp_env;
+                uint8_t* g = run_dst(kk, first - kk * ne);
+                const uint32_t mis = (uint32_t)reinterpret_cast<uintptr_t>(g) & 15u;
+                off += (mis - off) & 15u;
+                const uint8_t* src = stage + off;  // src = g mod 16
                 const uint32_t len = (end - first) * L.unp_env;
-                for (uint32_t b = (uint32_t)lane; b < len; b += 32u) gst_u8(g + b, src[b]);
+                const uint32_t head = min(len, (16u - mis) & 15u);
+                const uint32_t body = (len - head) >> 4, tail0 = head + 16u * body;
+                if ((uint32_t)lane < head) gst_u8(g + lane, src[lane]);
+                for (uint32_t c = (uint32_t)lane; c < body; c += 32u)
+                    st_cs_v4(g + head + 16u * c, *reinterpret_cast<const uint4*>(src + head + 16u * c));
+                if ((uint32_t)lane < len - tail0) gst_u8(g + tail0 + lane, src[tail0 + lane]);
+                off += len;
             }
             __syncwarp();  // the staging area is read before the next block writes it
         }

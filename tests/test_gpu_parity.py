@@ -55,6 +55,16 @@ def test_single_agent_packed_and_unpacked(form):
 
 
 @pytest.mark.parametrize("form", sorted(FORMS))
+def test_unpacked_export_every_radius(form):
+    """The unpacked bytes of windows of 1, 9, 25 and 49 bits a plane, the
+    envs' runs starting at every offset mod 16."""
+    for r, A, S in ((0, 3, 9), (1, 4, 12), (2, 2, 16), (3, 5, 20)):
+        descs = [W.env_desc(S, A, (A + 1) // 2, r, r, 40, "0.2", 3)]
+        compare_run(37, 50 + r, descs, 90, ring=200, env_id_base=5,
+                    flags=hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED | FORMS[form])
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
 def test_uneven_batch(form):
     descs = W.uneven_descs(1500, 3)
     compare_run(1500, 3, descs, 300, flags=hase.HASE_EXPORT_ACTIONS | FORMS[form])
