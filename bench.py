@@ -498,6 +498,46 @@ def engine_exports(eng):
     return [(k, v) for k, v in out if v.shape[1] > 0]
 
 
+def gpu_local_cpus():
+    """The CPUs NVML names as closest to the current CUDA device (read-only
+    query), intersected with this process's; None when unknown."""
+    import ctypes
+
+    import torch
+
+    try:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if nv.nvmlDeviceGetHandleByUUID(("GPU-%s" % props.uuid).encode(), ctypes.byref(h)) != 0:
+            return None
+        words = (ctypes.c_ulong * 64)()
+        if nv.nvmlDeviceGetCpuAffinity(h, ctypes.c_uint(64), words) != 0:
+            return None
+        bits = 8 * ctypes.sizeof(ctypes.c_ulong)
+        cpus = {bits * i + b for i in range(64) for b in range(bits) if (words[i] >> b) & 1}
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
+def pinned_near_gpu(make):
+    """Run make() (pinned host allocations) on the GPU-local CPUs, so that
+    the pages land in the memory next to the GPU's host link."""
+    cpus = gpu_local_cpus()
+    if not cpus:
+        return make(), "default placement"
+    old = os.sched_getaffinity(0)
+    try:
+        os.sched_setaffinity(0, cpus)
+        return make(), "allocated on the %d GPU-local CPUs (NVML affinity)" % len(cpus)
+    finally:
+        os.sched_setaffinity(0, old)
+
+
 def run_e2e(eng, c, run, stream, args):
     """The rollout through the public API with every step's outputs copied to
     pinned host memory inside the timed region: the steps of chunk k + 1 run
@@ -511,7 +551,10 @@ def run_e2e(eng, c, run, stream, args):
     ex = engine_exports(eng)
     per_step = sum(v.shape[1] * v.element_size() for _, v in ex)
     chunk = max(1, min(1000, run, (1 << 30) // per_step))  # pinned staging of at most 1 GiB a buffer
-    host = [[torch.empty((chunk, v.shape[1]), dtype=v.dtype, pin_memory=True) for _, v in ex] for _ in range(2)]
+    nbytes = chunk * per_step
+    (host, hst), placement = pinned_near_gpu(lambda: (
+        [[torch.empty((chunk, v.shape[1]), dtype=v.dtype, pin_memory=True) for _, v in ex] for _ in range(2)],
+        torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)))
     copy = torch.cuda.Stream()
     done_copy = {}  # ring chunk index -> event after its copy
     torch.cuda.synchronize()
@@ -550,9 +593,7 @@ def run_e2e(eng, c, run, stream, args):
     ms = t0.elapsed_time(t1)
     # the same bytes copied alone (pinned, one stream): the link's rate for this traffic
     v0 = ex[0][1]
-    nbytes = chunk * per_step
     dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
-    hst = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     for _ in range(2):
         hst.copy_(dev, non_blocking=True)
     torch.cuda.synchronize()
@@ -569,7 +610,7 @@ def run_e2e(eng, c, run, stream, args):
     achieved = per_step * n_steps / (ms / 1e3) / 1e9
     return {"value": eng.n_envs * n_steps / (ms / 1e3), "unit": "env-steps/s",
             "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(per_step),
-            "d2h_gbs": achieved, "d2h_link_peak_gbs": link, "link_frac": achieved / link,
+            "d2h_gbs": achieved, "d2h_link_peak_gbs": link, "link_frac": achieved / link, "host_memory": placement,
             "note": "per env-step: every output ring slot (%s) copied to pinned host memory, overlapped with the "
                     "next chunk's steps; link peak = the same chunk bytes copied alone" % ", ".join(k for k, _ in ex)}
 
