@@ -550,7 +550,10 @@ def run_e2e(eng, c, run, stream, args):
     n_steps = run * max(1, min(args.steps, 3))
     ex = engine_exports(eng)
     per_step = sum(v.shape[1] * v.element_size() for _, v in ex)
-    chunk = max(1, min(1000, run, (1 << 30) // per_step))  # pinned staging of at most 1 GiB a buffer
+    # chunks of at most 1,000 steps and 1 GiB of pinned staging a buffer, a
+    # divisor of the ring so that no chunk wraps round it (one copy per ring)
+    limit = max(1, min(1000, run, (1 << 30) // per_step))
+    chunk = max(d for d in range(1, limit + 1) if eng.ring % d == 0)
     nbytes = chunk * per_step
     (host, hst), placement = pinned_near_gpu(lambda: (
         [[torch.empty((chunk, v.shape[1]), dtype=v.dtype, pin_memory=True) for _, v in ex] for _ in range(2)],
