@@ -65,6 +65,16 @@ def test_unpacked_export_every_radius(form):
 
 
 @pytest.mark.parametrize("form", sorted(FORMS))
+def test_unpacked_export_uneven_and_waves(form):
+    """The unpacked export where a group's envs are not consecutive in the
+    layout (mixed shapes: written directly, not staged), and with more CTAs
+    than SMs (staged groups of one family, CTAs in waves)."""
+    fl = hase.HASE_EXPORT_ACTIONS | hase.HASE_EXPORT_UNPACKED | FORMS[form]
+    compare_run(60, 8, W.uneven_descs(60, 11), 45, ring=180, flags=fl)
+    compare_run(2600, 9, [W.env_desc(8, 2, 1, 2, 2, 20, "0.2", 1)], 25, ring=170, flags=fl, env_id_base=3)
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
 def test_uneven_batch(form):
     descs = W.uneven_descs(1500, 3)
     compare_run(1500, 3, descs, 300, flags=hase.HASE_EXPORT_ACTIONS | FORMS[form])
