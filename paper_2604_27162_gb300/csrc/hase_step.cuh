@@ -24,6 +24,8 @@
 //                       Philox actions of the next chunk.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -1362,7 +1364,12 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
         const uint32_t dlut = (64u - dn) | ((64u + dn) << 8) | (65u << 16) | (63u << 24);
         __syncwarp();
         // One step: claim, read, resolve, update.  g: step inside the launch.
-        auto step = [&](uint32_t a, uint16_t* Tk, uint32_t g) {
+        // ENDS: the step may end an episode (the launch step index g is checked
+        // against warp_next); a group of four steps that ends none runs the
+        // step without the check (measured: the check, with its warp barriers,
+        // cost ~30 cycles a step even when not taken).
+        auto step = [&](uint32_t a, uint16_t* Tk, uint32_t g, auto ends) {
+            constexpr bool ENDS = decltype(ends)::value;
             const uint32_t dd = __byte_perm(dlut, 0, 0x4440u | ((a + 3u) & 3u)) - 64u;
             const uint32_t tgt = p + dd;
             const uint32_t open = (nbr_cur >> a) & 1u;  // inside the grid, no obstacle (a = 0: never)
@@ -1383,8 +1390,8 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
             }
             p = won ? tgt : p;
             nbr_cur = won ? (tst & 0x1eu) : nbr_cur;
-            if (live) *Tk = (uint16_t)(p | (g == next_done ? kDoneBit : 0u));
-            if (g == warp_next) {  // some env of this warp ends its episode (a8)
+            if (live) *Tk = (uint16_t)(p | (ENDS && g == next_done ? kDoneBit : 0u));
+            if (ENDS && g == warp_next) {  // some env of this warp ends its episode (a8)
                 const bool done = g == next_done;
                 __syncwarp();
                 if (done) st8[p] = (uint8_t)nbr_cur;
@@ -1410,12 +1417,19 @@ __global__ void __launch_bounds__(MAXT, MINB) step_kernel(const StepParams P) {
                 uint32_t aw = live ? A[0] : 0u;
                 for (; k + 4 <= len; k += 4) {
                     const uint32_t aw_next = (live && k + 4 < len) ? A[((k + 4) >> 2) * nsl] : 0u;
+                    if (warp_next - (g0 + k) >= 4u) {  // no episode ends in these four steps (warp-uniform)
 #pragma unroll
-                    for (uint32_t j = 0; j < 4; ++j)
-                        step(__byte_perm(aw, 0, 0x4440u + j), T + (k + j) * nsl, g0 + k + j);
+                        for (uint32_t j = 0; j < 4; ++j)
+                            step(__byte_perm(aw, 0, 0x4440u + j), T + (k + j) * nsl, g0 + k + j, std::false_type{});
+                    } else {
+#pragma unroll
+                        for (uint32_t j = 0; j < 4; ++j)
+                            step(__byte_perm(aw, 0, 0x4440u + j), T + (k + j) * nsl, g0 + k + j, std::true_type{});
+                    }
                     aw = aw_next;
                 }
-                for (; k < len; ++k) step(__byte_perm(aw, 0, 0x4440u + (k & 3u)), T + k * nsl, g0 + k);
+                for (; k < len; ++k)
+                    step(__byte_perm(aw, 0, 0x4440u + (k & 3u)), T + k * nsl, g0 + k, std::true_type{});
             }
             __syncthreads();
         }

@@ -842,7 +842,11 @@ __global__ void __launch_bounds__(MAXT, 1) stream_kernel(const StepParams P) {
         // the rare step where some env of the warp ends its episode, the
         // reset).  Branch-free except for that warp-uniform case: a lane with
         // nothing to claim, read or write addresses its own scratch bytes.
-        auto step = [&](uint32_t a, uint32_t g) {
+        // ENDS: the step may end an episode; a quad that ends none runs the
+        // step without the check (with its warp barriers it cost ~30 cycles
+        // a step even when not taken).
+        auto step = [&](uint32_t a, uint32_t g, auto ends) {
+            constexpr bool ENDS = decltype(ends)::value;
             const uint32_t dd = __byte_perm(dlut, 0, 0x4440u | ((a + 3u) & 3u)) - 64u;
             const uint32_t tgt = p + dd;
             const bool open = (nbr >> a) & 1u;  // inside the grid, no obstacle (a = 0: never)
@@ -860,8 +864,8 @@ __global__ void __launch_bounds__(MAXT, 1) stream_kernel(const StepParams P) {
             sts8(won ? st_a + tgt : st_scr, tst | kOccBit);
             p = won ? tgt : p;
             nbr = won ? (tst & 0x1eu) : nbr;
-            sts16(rec_a + 2u * ((g & ring_mask) * slot_stride), p | ((g == next_done && agent0) ? 0x8000u : 0u));
-            if (g == warp_next) {  // some env of this warp ends its episode (a8)
+            sts16(rec_a + 2u * ((g & ring_mask) * slot_stride), p | ((ENDS && g == next_done && agent0) ? 0x8000u : 0u));
+            if (ENDS && g == warp_next) {  // some env of this warp ends its episode (a8)
                 const bool done = g == next_done;
                 __syncwarp();
                 if (done) sts8(st_a + p, nbr);
@@ -903,12 +907,15 @@ __global__ void __launch_bounds__(MAXT, 1) stream_kernel(const StepParams P) {
             }
             const uint32_t cur = lds32(act_a + (qr & (kActRing - 1u)) * act_row);
             const uint32_t j0 = (uint32_t)(t & 3u), len = min(4u - j0, n - g);
-            if (len == 4u) {
+            if (len == 4u && warp_next - g >= 4u) {  // no episode ends in this quad (warp-uniform)
 #pragma unroll
-                for (uint32_t j = 0; j < 4; ++j) step((cur >> (8 * j)) & 0xffu, g + j);
+                for (uint32_t j = 0; j < 4; ++j) step((cur >> (8 * j)) & 0xffu, g + j, std::false_type{});
+            } else if (len == 4u) {
+#pragma unroll
+                for (uint32_t j = 0; j < 4; ++j) step((cur >> (8 * j)) & 0xffu, g + j, std::true_type{});
             } else {
 #pragma unroll 1
-                for (uint32_t j = 0; j < len; ++j) step((cur >> (8 * (j0 + j))) & 0xffu, g + j);
+                for (uint32_t j = 0; j < len; ++j) step((cur >> (8 * (j0 + j))) & 0xffu, g + j, std::true_type{});
             }
             g += len;
             t += len;
