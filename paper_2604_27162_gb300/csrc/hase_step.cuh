@@ -876,6 +876,58 @@ __device__ __forceinline__ void st16(uint64_t* p, uint64_t a, uint64_t b) {
     *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(a, b);
 }
 
+// Global stores of 8, 16 and 32 bytes (CS: evict-first).
+template <bool CS>
+__device__ __forceinline__ void out8(uint64_t* p, uint64_t a) {
+    if (CS)
+        asm volatile("st.global.cs.u64 [%0], %1;" ::"l"(p), "l"(a));
+    else
+        *p = a;
+}
+template <bool CS>
+__device__ __forceinline__ void out16(uint64_t* p, uint64_t a, uint64_t b) {
+    if (CS)
+        asm volatile("st.global.cs.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b));
+    else
+        *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(a, b);
+}
+template <bool CS>
+__device__ __forceinline__ void out32(uint64_t* p, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    if (CS)
+        asm volatile("st.global.cs.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d));
+    else
+        asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d));
+}
+
+// Six consecutive output words at o (8-byte aligned) with as few stores as
+// the alignment allows: at a 32-byte boundary or 16 bytes past one, one
+// 32-byte and one 16-byte store (a store per 32-byte sector where it can:
+// the store path handles each lane's sectors one by one, and scattered
+// half-sector stores of the emission hold up the dynamics warps' shared
+// memory accesses; measured on 1024 envs x 10 agents, same GPU: +1.5 %, and
+// without any observation stores +7 %); otherwise 8 + 16 + 16 + 8 bytes, or
+// 8 + 32 + 8 at 24 bytes past a boundary.  (The streaming form keeps its
+// 16-byte stores: 32-byte ones measured 1.3 % slower there.)
+template <bool CS>
+__device__ __forceinline__ void out6(uint64_t* o, uint64_t w0, uint64_t w1, uint64_t w2, uint64_t w3, uint64_t w4,
+                                     uint64_t w5) {
+    const uint32_t q = (uint32_t)reinterpret_cast<uintptr_t>(o) & 31u;
+    if (!(q & 8u)) {
+        const bool q0 = q == 0u;
+        out32<CS>(q0 ? o : o + 2, q0 ? w0 : w2, q0 ? w1 : w3, q0 ? w2 : w4, q0 ? w3 : w5);
+        out16<CS>(q0 ? o + 4 : o, q0 ? w4 : w0, q0 ? w5 : w1);
+    } else {
+        out8<CS>(o, w0);
+        if (q == 24u) {
+            out32<CS>(o + 1, w1, w2, w3, w4);
+        } else {
+            out16<CS>(o + 1, w1, w2);
+            out16<CS>(o + 3, w3, w4);
+        }
+        out8<CS>(o + 5, w5);
+    }
+}
+
 // One team's observers.  With 16-byte aligned records (T.v16) the three
 // words of two consecutive observers leave as three 16-byte stores, and a
 // lone observer as one 16-byte and one 8-byte store; otherwise three 8-byte
@@ -898,9 +950,7 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
                 observer_words<A, TA, HI, W2, LOS>(T, a, R, D, KR, C2, KP, centre, centre_hi, X4, Y4, P4, P8, seenf);
             uint64_t* o = T.ob + 6 * (a - T.ai0);
             if (T.v16) {
-                st16(o, p.o0, p.o0h);
-                st16(o + 2, p.al, p.alh);
-                st16(o + 4, p.op, p.oph);
+                out6<false>(o, p.o0, p.o0h, p.al, p.alh, p.op, p.oph);
             } else {
                 o[0] = p.o0;
                 o[1] = p.o0h;
@@ -920,9 +970,7 @@ __device__ __forceinline__ void emit_team_fast(const TeamCtx& T, uint32_t R, con
             if (T.v16 && !(w & 1) && a + 1 < end) {
                 const Words3 q = observer_words<A, TA, HI, W2, LOS>(T, a + 1, R, D, KR, C2, KP, centre, centre_hi, X4, Y4,
                                                                P4, P8, seenf);
-                st16(o, p.o0, p.al);
-                st16(o + 2, p.op, q.o0);
-                st16(o + 4, q.al, q.op);
+                out6<false>(o, p.o0, p.al, p.op, q.o0, q.al, q.op);
                 a += 2;
             } else if (T.v16 && (w & 1)) {
                 o[0] = p.o0;
