@@ -437,6 +437,59 @@ def _full_size_check(cfg, n_steps, sample_envs, flags=0, setting=None, graph=Fal
     eng.close()
 
 
+def _full_size_exports_check(cfg, n_steps, sample_envs, flags):
+    """The optional exports at full size, sampled: every step of the sampled
+    envs' centralized observation, true state and fog of war against a
+    one-env oracle (with the desynchronised start when asked: its offsets
+    and pre-steps depend on the env id only)."""
+    import torch
+
+    n = cfg["n_envs"]
+    descs = cfg["descs"]
+    eng = hase.Engine(n, cfg["seed"], descs, n_steps, flags)
+    eng.step(n_steps)
+    torch.cuda.synchronize()
+    L = eng.layout
+    nxt = lambda off, total, e: int(off[e + 1]) if e + 1 < n else total
+    fog = 0 if not flags & hase.HASE_EXPORT_FOG else (2 if flags & hase.HASE_FOG_PER_AGENT else 1)
+    aoff = L["agent_off"].astype(np.int64)
+    for e in sample_envs:
+        d = descs[0 if len(descs) == 1 else e]
+        w = oracle.World(1, cfg["seed"], [d], env_id_base=e, desync=bool(flags & hase.HASE_DESYNC_START), fog=fog)
+        obs = eng.obs[:, int(L["obs_off"][e]):nxt(L["obs_off"], eng.obs.shape[1], e)].cpu().numpy().view(np.uint64)
+        cen = fo = cells = ept = None
+        if eng.central is not None:
+            c0 = int(L["central_off"][e])
+            cen = eng.central[:, c0:nxt(L["central_off"], eng.central.shape[1], e)].cpu().numpy().view(np.uint64)
+        if eng.fog is not None:
+            f0 = int(L["fog_off"][e])
+            fo = eng.fog[:, f0:nxt(L["fog_off"], eng.fog.shape[1], e)].cpu().numpy().view(np.uint64)
+        if eng.cells is not None:
+            cells = eng.cells[:, aoff[e]:aoff[e + 1]].cpu().numpy().view(np.uint16)
+            ept = eng.ep_t[:, e].cpu().numpy().view(np.uint32)
+        for t in range(n_steps):
+            o = w.step()
+            assert (obs[t] == o["obs"]).all(), (e, t)
+            if cen is not None:
+                assert (cen[t] == w.central()).all(), (e, t)
+            if fo is not None:
+                assert (fo[t] == w.fog()).all(), (e, t)
+            if cells is not None:
+                c, ep = w.true_state()
+                assert (cells[t] == c).all() and ept[t] == ep[0], (e, t)
+    eng.close()
+
+
+def test_full_size_optional_exports_sampled():
+    """ten1k at the benchmark's size with the centralized observation, the
+    true state and the desynchronised start, then with the per-agent fog of
+    war, each sampled on four envs over 1,500 steps."""
+    cfg = W.ten1k()
+    _full_size_exports_check(cfg, 1500, [0, 5, 512, 1023],
+                             hase.HASE_EXPORT_CENTRAL | hase.HASE_EXPORT_STATE | hase.HASE_DESYNC_START)
+    _full_size_exports_check(cfg, 1500, [1, 700, 1022], hase.HASE_EXPORT_FOG | hase.HASE_FOG_PER_AGENT)
+
+
 def test_full_size_ten_agents_sampled():
     cfg = W.ten1k()
     _full_size_check(cfg, cfg["steps"], [0, 1, 337, 511, 512, 1023])
